@@ -1,0 +1,147 @@
+/*
+ * rfnse.h -- C ABI of the GB300 (sm_103a) tau-preconditioned GMRES time stepper for the Riesz
+ * fractional nonlinear Schroedinger equation
+ *
+ *     i u_t + d^alpha u / d|x|^alpha + rho |u|^2 u = 0,   1 < alpha <= 2,  rho >= 0,
+ *
+ * on a box with homogeneous Dirichlet data (Chen, Yang, Zhang, "Sine-transform-based fast solvers
+ * for Riesz fractional nonlinear Schroedinger equations with attractive nonlinearities",
+ * arXiv 2410.03643; Sec. 2 for the discretisation, Sec. 3-4 for the solver).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * Grid: axis a in {0 (x), 1 (y), 2 (z)} has n[a] interior points x_j = lo[a] + j h_a, j = 1..n[a],
+ *   h_a = (hi[a] - lo[a]) / (n[a] + 1)  (Sec. 2.1).  n[a] + 1 must be a power of two in [4, 2048]:
+ *   the fast sine transform (Sec. 4, "FST") is computed from a power-of-two FFT of length 2(n+1).
+ * Layout: a grid function is N = n[0]*n[1]*n[2] complex numbers, interleaved FP64 (re, im), with
+ *   x fastest: index = j_x + n[0]*(j_y + n[1]*j_z).  This is the column-stacking vec of Sec. 2.2.
+ * Real block form: the paper's real vectors x = [z; y] (Sec. 3, u = y + i z) are stored as the
+ *   complex vector y + i z; the real inner product of Sec. 3 is Re(a^H b).
+ * Pointers: "device" arguments are CUDA device pointers of the current device; "host" arguments
+ *   are ordinary host memory.  The caller owns every buffer it passes; the library owns only its
+ *   context and workspace.  Buffers must not overlap unless stated.
+ * Streams: all device work is issued on the stream given to rfnse_create (NULL = legacy default
+ *   stream).  Entry points that return statistics to the host synchronise that stream.
+ * Errors: every call returns an rfnse_status; no C++ exception crosses the ABI.  After an error,
+ *   rfnse_last_error(ctx) describes it.  RFNSE_ENOCONV still writes the best iterate.
+ */
+#ifndef RFNSE_H
+#define RFNSE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rfnse_ctx rfnse_ctx;
+
+typedef enum {
+  RFNSE_OK = 0,
+  RFNSE_EINVAL = 1,   /* invalid argument (sizes, parameters, null pointers) */
+  RFNSE_ENOMEM = 2,   /* device or pinned host allocation failed */
+  RFNSE_ECUDA = 3,    /* a CUDA runtime call failed */
+  RFNSE_ENOCONV = 4,  /* GMRES reached max_it before the tolerance (best iterate returned) */
+  RFNSE_ENUMERIC = 5, /* a non-finite value appeared in a residual or Arnoldi norm */
+  RFNSE_ETIMEOUT = 6  /* reserved: a bounded device-side wait gave up */
+} rfnse_status;
+
+typedef struct {
+  int d;              /* space dimension, 1..3 */
+  int n[3];           /* interior points per axis (n[a] + 1 a power of two, 4..2048); unused axes ignored */
+  double lo[3], hi[3];/* box [lo, hi] per axis, hi > lo */
+  double alpha;       /* Riesz order, 1 < alpha <= 2 */
+  double rho;         /* nonlinearity strength, >= 0 */
+  double dt;          /* time step, > 0 */
+  double omega;       /* TBAN iteration parameter of the preconditioner, > 0 (the paper fixes 1) */
+  int restart;        /* GMRES restart length m, 1..64 */
+  int max_it;         /* maximum Arnoldi steps per linear solve (the paper uses 2000) */
+  double tol;         /* stop when the relative residual ||f - R x|| / ||f|| < tol */
+  int precision;      /* 0 = FP64 throughout; 1 = mixed: FP32 transforms inside an FGMRES inner
+                         solve, FP64 Arnoldi/Givens, FP64 outer residual with iterative refinement */
+  int first_step;     /* 0 = predictor only, 1 = predictor-corrector Crank-Nicolson first step */
+  double inner_tol;   /* mixed form: relative tolerance of each inner solve (<= 0: 1e-6) */
+  int max_outer;      /* mixed form: maximum refinement steps per solve (<= 0: 30) */
+} rfnse_params;
+
+/* Fill p with defaults: d=1, n=255, box [-20,20], alpha=1.5, rho=2, dt=0.01, omega=1, restart=20,
+   max_it=2000, tol=1e-10, precision=0, first_step=1, inner_tol=1e-6, max_outer=30. */
+void rfnse_default_params(rfnse_params* p);
+
+/* Create a solver context for the problem p (Sec. 2: grid, alpha, rho, dt) on the current CUDA
+   device.  stream is a cudaStream_t (may be NULL).  Allocates the device workspace (Krylov basis
+   of restart+1 vectors and about ten work vectors of N complex FP64 values; the mixed form adds
+   restart+2 FP32 vectors) and computes, on the device, the coefficients c_k of eq. 'coefficients'
+   (Sec. 2.1), the tau eigenvalues of eq. 'taudiagonal' (Sec. 4) per axis, and the circulant
+   eigenvalues used for the Toeplitz products.  On success *out receives the context; on failure
+   *out is NULL.  Errors: EINVAL, ENOMEM, ECUDA. */
+int rfnse_create(const rfnse_params* p, void* stream, rfnse_ctx** out);
+
+/* Release the context and its workspace (NULL is accepted). */
+void rfnse_destroy(rfnse_ctx* ctx);
+
+/* Text of the last error of ctx ("" if none); valid until the next call on ctx. */
+const char* rfnse_last_error(const rfnse_ctx* ctx);
+
+/* N = number of complex grid unknowns of the context. */
+long long rfnse_size(const rfnse_ctx* ctx);
+
+/* Load the time-stepping state.  step = 0: u_cur = u^0 (initial data on the grid, Sec. 2.1) and
+   u_prev is ignored (may be NULL).  step >= 1: (u_prev, u_cur) = (u^{step-1}, u^{step}), e.g. to
+   resume from rfnse_get_state.  on_device = 1: device pointers; 0: host pointers.  Each holds N
+   complex FP64 values.  Errors: EINVAL, ECUDA. */
+int rfnse_set_state(rfnse_ctx* ctx, const void* u_prev, const void* u_cur, int step, int on_device);
+
+/* Read the state (u^{step-1}, u^{step}) and step.  u_prev is not written when step == 0.  Either
+   pointer may be NULL.  Errors: EINVAL, ECUDA. */
+int rfnse_get_state(rfnse_ctx* ctx, void* u_prev, void* u_cur, int* step, int on_device);
+
+/* Advance nsteps time steps of the three-level linearly implicit scheme (Sec. 2.1 eq.
+   'discretizedRFSE', Sec. 2.2 eq. 'discretizedRFSE2D'; the same Kronecker-sum form for d = 3).
+   Step n >= 1 solves (D - T + iI) u^{n+1} = (T - D + iI) u^{n-1}, D = rho dt |u^n|^2, by GMRES
+   with the sine-transform TBAN preconditioner (Sec. 4 eq. 'taupre'), zero initial guess (Sec. 5).
+   The first step (step 0 -> 1) is the Crank-Nicolson step with mu -> mu/2, D -> rho (dt/2)|u~|^2,
+   u~ = u^0 (predictor) and, if first_step = 1, u~ = (u^0 + u^1*)/2 (corrector).
+   traj (may be NULL): nsteps * N complex FP64, receives u^{step+1} .. u^{step+nsteps}.
+   iters (host, may be NULL): nsteps ints, Arnoldi steps per time step (inner steps for the mixed
+   form; predictor + corrector for the first step).  relres (host, may be NULL): nsteps doubles,
+   final relative residual estimate per step.  on_device refers to traj only.
+   Errors: EINVAL, ECUDA, ENOCONV (the step is still taken), ENUMERIC. */
+int rfnse_run(rfnse_ctx* ctx, int nsteps, void* traj, int* iters, double* relres, int on_device);
+
+/* ---- building blocks (device pointers; used by the parity tests) ---------------------------- */
+
+/* out = (D - T + iI) u, the system matrix of eq. 'equ3' (Sec. 2).  half = 1 uses mu_a/2 (first
+   step).  u, out: N complex FP64 (may not alias); D: N FP64.  Errors: EINVAL, ECUDA. */
+int rfnse_apply_A(rfnse_ctx* ctx, const void* u, void* out, const double* D, int half);
+
+/* z = F~^{-1} v for F~ = (1/(2w)) [wI + tau(T_d)] (wI + D_d) of eq. 'taupre' (Sec. 4), in the
+   complex storage of the real block vectors.  precision 0: FP64 transforms; 1: FP32 transforms
+   (input and output still FP64).  v, z: N complex FP64 (may not alias); D: N FP64. */
+int rfnse_apply_prec(rfnse_ctx* ctx, const void* v, void* z, const double* D, int half, int precision);
+
+/* out = S in along one axis: the orthonormal DST-I [S]_{jk} = sqrt(2/(n+1)) sin(pi jk/(n+1))
+   (Sec. 4, after eq. 'taudiagonal'), applied to every grid line of that axis.  precision 0/1 as
+   above.  in, out: N complex FP64, may not alias. */
+int rfnse_dst(rfnse_ctx* ctx, int axis, const void* in, void* out, int precision);
+
+/* out = mu_a T_0 in along one axis: the symmetric Toeplitz matrix of eq. 'equ2' with first row
+   c_0..c_{n-1} (Sec. 2.1), mu_a = dt / h_a^alpha (halved when half = 1), on every grid line of
+   that axis.  FP64.  in, out: N complex FP64, may not alias. */
+int rfnse_toeplitz(rfnse_ctx* ctx, int axis, const void* in, void* out, int half);
+
+/* Solve (D - T + iI) u = b (eq. 'equ3') by right-preconditioned GMRES(restart) from u = 0 with the
+   context's tolerance and precision (the real block form of Sec. 3, eq. 'positiveBlockForm').
+   b, u: N complex FP64 (may not alias); D: N FP64; iters, relres: host, may be NULL.
+   Errors: EINVAL, ECUDA, ENOCONV, ENUMERIC. */
+int rfnse_solve(rfnse_ctx* ctx, const double* D, const void* b, void* u, int half, int* iters,
+                double* relres);
+
+/* Copy the FCD coefficients c_0..c_{nmax-1} (nmax = largest n[a]) and the tau eigenvalues of T_0
+   (not scaled by mu_a) of every axis, axis after axis (sum of n[a] values), to host memory.
+   Either pointer may be NULL. */
+int rfnse_get_coefficients(rfnse_ctx* ctx, double* c, double* lam);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RFNSE_H */

@@ -1,0 +1,312 @@
+// C ABI (include/rfnse.h): context life cycle, state, time stepping and building blocks.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+#include "internal.cuh"
+#include "solve.cuh"
+
+using namespace rfnse;
+
+namespace {
+
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int ilog2(long long v) {
+  int r = 0;
+  while ((1LL << r) < v) ++r;
+  return r;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return cudaSuccess;
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+void free_ctx(rfnse_ctx* c) {
+  if (!c) return;
+  cudaFree(c->c);
+  for (int a = 0; a < 3; ++a) {
+    cudaFree(c->lam[a]);
+    cudaFree(c->circ[a]);
+    cudaFree(c->tw64[a]);
+    cudaFree(c->tw32[a]);
+    cudaFree(c->u[a]);
+  }
+  cudaFree(c->D);
+  cudaFree(c->f);
+  cudaFree(c->x);
+  cudaFree(c->w);
+  cudaFree(c->r);
+  cudaFree(c->t1);
+  cudaFree(c->t2);
+  cudaFree(c->zb);
+  cudaFree(c->V);
+  cudaFree(c->Z32);
+  cudaFree(c->t1f);
+  cudaFree(c->t2f);
+  cudaFree(c->partials);
+  cudaFree(c->counter);
+  cudaFree(c->gs);
+  if (c->peek) cudaFreeHost(c->peek);
+  delete c;
+}
+
+const char* validate(const rfnse_params* p) {
+  if (!p) return "params is NULL";
+  if (p->d < 1 || p->d > 3) return "d must be 1, 2 or 3";
+  for (int a = 0; a < p->d; ++a) {
+    if (p->n[a] < 3 || p->n[a] > 2047 || !is_pow2((long long)p->n[a] + 1))
+      return "n[a] + 1 must be a power of two between 4 and 2048";
+    if (!(p->hi[a] > p->lo[a]) || !std::isfinite(p->hi[a] - p->lo[a])) return "need hi[a] > lo[a]";
+  }
+  if (!(p->alpha > 1.0 && p->alpha <= 2.0)) return "alpha must satisfy 1 < alpha <= 2";
+  if (!(p->rho >= 0.0) || !std::isfinite(p->rho)) return "rho must be finite and >= 0";
+  if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return "dt must be finite and > 0";
+  if (!(p->omega > 0.0) || !std::isfinite(p->omega)) return "omega must be finite and > 0";
+  if (p->restart < 1 || p->restart > kMaxM) return "restart must be in 1..64";
+  if (p->max_it < 1) return "max_it must be >= 1";
+  if (!(p->tol > 0.0)) return "tol must be > 0";
+  if (p->precision != 0 && p->precision != 1) return "precision must be 0 (FP64) or 1 (mixed)";
+  if (p->first_step != 0 && p->first_step != 1) return "first_step must be 0 or 1";
+  return nullptr;
+}
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+extern "C" {
+
+void rfnse_default_params(rfnse_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->d = 1;
+  p->n[0] = p->n[1] = p->n[2] = 255;
+  for (int a = 0; a < 3; ++a) {
+    p->lo[a] = -20.0;
+    p->hi[a] = 20.0;
+  }
+  p->alpha = 1.5;
+  p->rho = 2.0;
+  p->dt = 0.01;
+  p->omega = 1.0;
+  p->restart = 20;
+  p->max_it = 2000;
+  p->tol = 1e-10;
+  p->precision = 0;
+  p->first_step = 1;
+  p->inner_tol = 1e-6;
+  p->max_outer = 30;
+}
+
+int rfnse_create(const rfnse_params* p, void* stream, rfnse_ctx** out) {
+  if (!out) return RFNSE_EINVAL;
+  *out = nullptr;
+  if (const char* why = validate(p)) {
+    g_create_error = why;
+    return RFNSE_EINVAL;
+  }
+  rfnse_ctx* c = new (std::nothrow) rfnse_ctx();
+  if (!c) return RFNSE_ENOMEM;
+  c->p = *p;
+  c->stream = (cudaStream_t)stream;
+  c->d = p->d;
+  c->N = 1;
+  int nmax = 0;
+  for (int a = 0; a < 3; ++a) {
+    c->n[a] = (a < c->d) ? p->n[a] : 1;
+    c->stride[a] = c->N;
+    c->N *= c->n[a];
+    if (a < c->d) {
+      c->L[a] = 2 * (c->n[a] + 1);
+      c->log2L[a] = ilog2(c->L[a]);
+      c->h[a] = (p->hi[a] - p->lo[a]) / (c->n[a] + 1);
+      c->mu[a] = p->dt / std::pow(c->h[a], p->alpha);
+      if (c->n[a] > nmax) nmax = c->n[a];
+    } else {
+      c->L[a] = 0;
+      c->log2L[a] = 0;
+      c->h[a] = 0.0;
+      c->mu[a] = 0.0;
+    }
+  }
+  const long long N = c->N;
+  const int m = p->restart;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) {
+    if (e == cudaSuccess && r != cudaSuccess) e = r;
+  };
+  chk(dalloc(&c->c, nmax));
+  for (int a = 0; a < c->d; ++a) {
+    chk(dalloc(&c->lam[a], c->n[a]));
+    chk(dalloc(&c->circ[a], c->L[a]));
+    chk(dalloc(&c->tw64[a], c->L[a]));
+    chk(dalloc(&c->tw32[a], c->L[a]));
+  }
+  for (int i = 0; i < 3; ++i) chk(dalloc(&c->u[i], N));
+  chk(dalloc(&c->D, N));
+  chk(dalloc(&c->f, N));
+  chk(dalloc(&c->x, N));
+  chk(dalloc(&c->w, N));
+  chk(dalloc(&c->r, N));
+  chk(dalloc(&c->t1, N));
+  chk(dalloc(&c->t2, N));
+  chk(dalloc(&c->zb, N));
+  chk(dalloc(&c->V, (size_t)(m + 1) * N));
+  chk(dalloc(&c->t1f, N));
+  chk(dalloc(&c->t2f, N));
+  if (p->precision == 1) chk(dalloc(&c->Z32, (size_t)m * N));
+  c->red_blocks = choose_reduce_blocks(N);
+  chk(dalloc(&c->partials, 1024));
+  chk(dalloc(&c->counter, 1));
+  chk(dalloc(&c->gs, 1));
+  if (e == cudaSuccess) chk(cudaMallocHost((void**)&c->peek, sizeof(GmresPeek)));
+  if (e != cudaSuccess) {
+    g_create_error = std::string("allocation failed: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    free_ctx(c);
+    return (e == cudaErrorMemoryAllocation) ? RFNSE_ENOMEM : RFNSE_ECUDA;
+  }
+  chk(cudaMemsetAsync(c->counter, 0, sizeof(unsigned), c->stream));
+  chk(cudaMemsetAsync(c->gs, 0, sizeof(GmresState), c->stream));
+  chk(cudaMemsetAsync(c->u[0], 0, sizeof(double2) * N, c->stream));
+  chk(cudaMemsetAsync(c->u[1], 0, sizeof(double2) * N, c->stream));
+  launch_setup_coefficients(c->c, nmax, p->alpha, c->stream);
+  for (int a = 0; a < c->d; ++a)
+    launch_setup_axis(c->c, c->n[a], c->L[a], c->lam[a], c->circ[a], c->tw64[a], c->tw32[a], c->stream);
+  chk(cudaGetLastError());
+  chk(cudaStreamSynchronize(c->stream));
+  if (e != cudaSuccess) {
+    g_create_error = std::string("set-up failed: ") + cudaGetErrorString(e);
+    free_ctx(c);
+    return RFNSE_ECUDA;
+  }
+  *out = c;
+  return RFNSE_OK;
+}
+
+void rfnse_destroy(rfnse_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  free_ctx(ctx);
+}
+
+const char* rfnse_last_error(const rfnse_ctx* ctx) {
+  if (!ctx) return g_create_error.c_str();
+  return ctx->err.c_str();
+}
+
+long long rfnse_size(const rfnse_ctx* ctx) { return ctx ? ctx->N : 0; }
+
+int rfnse_set_state(rfnse_ctx* c, const void* u_prev, const void* u_cur, int step, int on_device) {
+  if (!c) return RFNSE_EINVAL;
+  if (!u_cur || step < 0 || (step > 0 && !u_prev)) {
+    c->err = "rfnse_set_state: u_cur required; u_prev required when step > 0";
+    return RFNSE_EINVAL;
+  }
+  const size_t bytes = sizeof(double2) * (size_t)c->N;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  c->iprev = 0;
+  c->icur = 1;
+  if (step > 0) RFNSE_CUDA_TRY(c, cudaMemcpyAsync(c->u[c->iprev], u_prev, bytes, kind, c->stream));
+  RFNSE_CUDA_TRY(c, cudaMemcpyAsync(c->u[c->icur], u_cur, bytes, kind, c->stream));
+  RFNSE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->step = step;
+  return RFNSE_OK;
+}
+
+int rfnse_get_state(rfnse_ctx* c, void* u_prev, void* u_cur, int* step, int on_device) {
+  if (!c) return RFNSE_EINVAL;
+  const size_t bytes = sizeof(double2) * (size_t)c->N;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (u_prev && c->step > 0) RFNSE_CUDA_TRY(c, cudaMemcpyAsync(u_prev, c->u[c->iprev], bytes, kind, c->stream));
+  if (u_cur) RFNSE_CUDA_TRY(c, cudaMemcpyAsync(u_cur, c->u[c->icur], bytes, kind, c->stream));
+  RFNSE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (step) *step = c->step;
+  return RFNSE_OK;
+}
+
+int rfnse_run(rfnse_ctx* c, int nsteps, void* traj, int* iters, double* relres, int on_device) {
+  if (!c || nsteps < 0) return RFNSE_EINVAL;
+  const size_t bytes = sizeof(double2) * (size_t)c->N;
+  int worst = RFNSE_OK;
+  for (int s = 0; s < nsteps; ++s) {
+    int it = 0;
+    double rr = 0.0;
+    const rfnse_status st = time_step(c, &it, &rr);
+    if (st != RFNSE_OK && st != RFNSE_ENOCONV) return st;
+    if (st == RFNSE_ENOCONV) worst = RFNSE_ENOCONV;
+    if (iters) iters[s] = it;
+    if (relres) relres[s] = rr;
+    if (traj) {
+      char* dst = (char*)traj + (size_t)s * bytes;
+      RFNSE_CUDA_TRY(c, cudaMemcpyAsync(dst, c->u[c->icur], bytes,
+                                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    }
+  }
+  RFNSE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return worst;
+}
+
+int rfnse_apply_A(rfnse_ctx* c, const void* u, void* out, const double* D, int half) {
+  if (!c || !u || !out || !D || u == out) return RFNSE_EINVAL;
+  RFNSE_CUDA_TRY(c, run_apply_A(c, (const double2*)u, (double2*)out, D, half ? 1 : 0));
+  RFNSE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return RFNSE_OK;
+}
+
+int rfnse_apply_prec(rfnse_ctx* c, const void* v, void* z, const double* D, int half, int precision) {
+  if (!c || !v || !z || !D || v == z || (precision != 0 && precision != 1)) return RFNSE_EINVAL;
+  RFNSE_CUDA_TRY(c, run_apply_prec(c, (const double2*)v, (double2*)z, D, half ? 1 : 0, precision));
+  RFNSE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return RFNSE_OK;
+}
+
+int rfnse_dst(rfnse_ctx* c, int axis, const void* in, void* out, int precision) {
+  if (!c || !in || !out || in == out || axis < 0 || axis >= c->d || (precision != 0 && precision != 1))
+    return RFNSE_EINVAL;
+  RFNSE_CUDA_TRY(c, run_dst(c, axis, (const double2*)in, (double2*)out, precision));
+  RFNSE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return RFNSE_OK;
+}
+
+int rfnse_toeplitz(rfnse_ctx* c, int axis, const void* in, void* out, int half) {
+  if (!c || !in || !out || in == out || axis < 0 || axis >= c->d) return RFNSE_EINVAL;
+  RFNSE_CUDA_TRY(c, run_toeplitz(c, axis, (const double2*)in, (double2*)out, half ? 1 : 0));
+  RFNSE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return RFNSE_OK;
+}
+
+int rfnse_solve(rfnse_ctx* c, const double* D, const void* b, void* u, int half, int* iters, double* relres) {
+  if (!c || !D || !b || !u || b == u) return RFNSE_EINVAL;
+  launch_neg_i((const double2*)b, c->f, c->N, c->stream);  // f = -i b  (Sec. 3: f = [-p; q])
+  int it = 0;
+  double rr = 0.0;
+  const rfnse_status st = solve_block(c, D, c->f, (double2*)u, half ? 1 : 0, &it, &rr);
+  RFNSE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (iters) *iters = it;
+  if (relres) *relres = rr;
+  return st;
+}
+
+int rfnse_get_coefficients(rfnse_ctx* c, double* cc, double* lam) {
+  if (!c) return RFNSE_EINVAL;
+  int nmax = 0;
+  for (int a = 0; a < c->d; ++a) nmax = c->n[a] > nmax ? c->n[a] : nmax;
+  if (cc) RFNSE_CUDA_TRY(c, cudaMemcpyAsync(cc, c->c, sizeof(double) * nmax, cudaMemcpyDeviceToHost, c->stream));
+  if (lam) {
+    size_t off = 0;
+    for (int a = 0; a < c->d; ++a) {
+      RFNSE_CUDA_TRY(c, cudaMemcpyAsync(lam + off, c->lam[a], sizeof(double) * c->n[a], cudaMemcpyDeviceToHost,
+                                        c->stream));
+      off += c->n[a];
+    }
+  }
+  RFNSE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return RFNSE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,112 @@
+// Library-internal declarations: the context, the device-resident GMRES state and the kernels
+// shared between translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdio>
+#include <string>
+#include "../../include/rfnse.h"
+
+namespace rfnse {
+
+constexpr int kMaxM = 64;  // largest supported restart length
+
+// Device-resident Arnoldi / Givens state of one GMRES cycle.  H is stored by columns:
+// H(i, j) = H[j * (kMaxM + 1) + i].
+struct GmresState {
+  // --- prefix read by the host (GmresPeek) ---
+  double beta;      // norm of the residual that starts the cycle
+  double relres;    // |g_{j+1}| / ref after the last Givens update
+  int done;         // 0 running, 1 converged, 2 exact breakdown, 3 non-finite value
+  int pad_;
+  // --- device-only ---
+  double inv_beta;  // 1 / beta
+  double ref;       // reference norm of the relative residual test
+  double tol;       // stop when |g_{j+1}| / ref < tol
+  double inv_h;     // 1 / h_{j+1,j}
+  double H[(kMaxM + 1) * kMaxM];
+  double cs[kMaxM], sn[kMaxM], g[kMaxM + 1], y[kMaxM];
+};
+
+// Host-visible copy of the prefix of GmresState that the control loop reads.
+struct GmresPeek {
+  double beta, relres;
+  int done, pad_;
+};
+
+inline int choose_reduce_blocks(long long N) {
+  long long b = (N + 2047) / 2048;
+  if (b < 1) b = 1;
+  if (b > 1024) b = 1024;
+  return (int)b;
+}
+
+// ---- Krylov / pointwise kernels (krylov.cu) -----------------------------------------------------
+// All reductions are deterministic: fixed grid, per-block partials, the last block to finish sums
+// the partials in block order.
+void launch_dot_axpy(const double2* vi, double2* w, const double2* vprev, const double* hprev, double* out,
+                     long long N, int blocks, double* partials, unsigned* counter, cudaStream_t s);
+void launch_norm_givens(const double2* vj, double2* w, const double* hjj, GmresState* gs, int j, long long N,
+                        int blocks, double* partials, unsigned* counter, cudaStream_t s);
+void launch_norm(const double2* x, GmresState* gs, long long N, int blocks, double* partials, unsigned* counter,
+                 cudaStream_t s);
+void launch_backsolve(GmresState* gs, int k, cudaStream_t s);
+void launch_combine(const double2* V, long long ldv, const GmresState* gs, int k, double2* out, long long N,
+                    cudaStream_t s);
+void launch_combine_f32_add(const float2* Z, long long ldz, const GmresState* gs, int k, double2* x, long long N,
+                            cudaStream_t s);
+void launch_diag(const double2* u, const double2* u2, double* D, double rho_dt, long long N, cudaStream_t s);
+void launch_neg_i(const double2* b, double2* f, long long N, cudaStream_t s);
+void launch_zero(double2* x, long long N, cudaStream_t s);
+void launch_start_cycle(GmresState* gs, double ref, double tol, cudaStream_t s);
+
+// ---- setup kernels (setup.cu) -------------------------------------------------------------------
+void launch_setup_coefficients(double* c, int nmax, double alpha, cudaStream_t s);
+void launch_setup_axis(const double* c, int n, int L, double* lam, double* circ, double2* tw64, float2* tw32,
+                       cudaStream_t s);
+
+}  // namespace rfnse
+
+// The opaque context of the C ABI.
+struct rfnse_ctx {
+  rfnse_params p;
+  cudaStream_t stream;
+  int d;
+  int n[3];
+  long long stride[3];
+  int L[3], log2L[3];
+  long long N;
+  double h[3], mu[3];
+  // coefficients (device)
+  double* c = nullptr;
+  double* lam[3] = {nullptr, nullptr, nullptr};
+  double* circ[3] = {nullptr, nullptr, nullptr};
+  double2* tw64[3] = {nullptr, nullptr, nullptr};
+  float2* tw32[3] = {nullptr, nullptr, nullptr};
+  // time-stepping state (device)
+  double2* u[3] = {nullptr, nullptr, nullptr};
+  int iprev = 0, icur = 1, step = 0;
+  double* D = nullptr;
+  // work vectors (device)
+  double2 *f = nullptr, *x = nullptr, *w = nullptr, *r = nullptr, *t1 = nullptr, *t2 = nullptr, *zb = nullptr;
+  double2* V = nullptr;     // (m + 1) Krylov vectors
+  float2* Z32 = nullptr;    // m preconditioned vectors of the mixed form
+  float2 *t1f = nullptr, *t2f = nullptr;
+  double* partials = nullptr;
+  unsigned* counter = nullptr;
+  int red_blocks = 1;
+  rfnse::GmresState* gs = nullptr;
+  rfnse::GmresPeek* peek = nullptr;  // pinned host
+  // per-step statistics of the last solve
+  int last_iters = 0, last_outer = 0;
+  double last_relres = 0.0;
+  std::string err;
+};
+
+#define RFNSE_CUDA_TRY(ctx, expr)                                                              \
+  do {                                                                                          \
+    cudaError_t e__ = (expr);                                                                   \
+    if (e__ != cudaSuccess) {                                                                   \
+      (ctx)->err = std::string(#expr) + ": " + cudaGetErrorString(e__);                         \
+      return RFNSE_ECUDA;                                                                       \
+    }                                                                                           \
+  } while (0)

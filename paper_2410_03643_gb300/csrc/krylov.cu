@@ -1,0 +1,260 @@
+// Arnoldi (modified Gram-Schmidt), Givens and pointwise kernels of the GMRES solve (paper Sec. 5,
+// "PGMRES").  Krylov vectors are complex FP64 with the real inner product <a, b> = Re(a^H b), which
+// is the Euclidean inner product of the real block vectors [Im; Re] of Sec. 3.
+#include <cmath>
+#include "internal.cuh"
+#include "cplx.cuh"
+
+namespace rfnse {
+
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+  if (warp == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  return v;  // valid in thread 0
+}
+
+// Store this block's partial; return true in every thread of the last block to arrive, which then
+// owns the final fixed-order sum.
+__device__ __forceinline__ bool arrive_last(double part, double* partials, unsigned* counter) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = part;
+    __threadfence();
+    const unsigned t = atomicAdd(counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  return last;
+}
+
+__device__ __forceinline__ double final_sum(const double* partials, unsigned* counter, double* sh) {
+  __threadfence();
+  double v = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += ((volatile const double*)partials)[i];
+  v = block_sum(v, sh);
+  if (threadIdx.x == 0) *counter = 0u;
+  return v;
+}
+
+// w -= (*hprev) vprev (if vprev), then out = <vi, w>.
+__global__ void __launch_bounds__(kRedThreads) k_dot_axpy(const double2* __restrict__ vi, double2* __restrict__ w,
+                                                          const double2* __restrict__ vprev,
+                                                          const double* hprev, double* out, long long N,
+                                                          double* partials, unsigned* counter) {
+  __shared__ double sh[32];
+  const double h = vprev ? *hprev : 0.0;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    double2 wv = w[i];
+    if (vprev) {
+      const double2 pv = vprev[i];
+      wv.x -= h * pv.x;
+      wv.y -= h * pv.y;
+      w[i] = wv;
+    }
+    const double2 a = vi[i];
+    acc += a.x * wv.x + a.y * wv.y;
+  }
+  const double part = block_sum(acc, sh);
+  if (arrive_last(part, partials, counter)) {
+    const double s = final_sum(partials, counter, sh);
+    if (threadIdx.x == 0) *out = s;
+  }
+}
+
+// w -= h_jj v_j; h_{j+1,j} = ||w||; Givens update of column j; convergence test.
+__global__ void __launch_bounds__(kRedThreads) k_norm_givens(const double2* __restrict__ vj, double2* __restrict__ w,
+                                                             const double* hjj, GmresState* gs, int j, long long N,
+                                                             double* partials, unsigned* counter) {
+  __shared__ double sh[32];
+  const double h = *hjj;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    double2 wv = w[i];
+    const double2 pv = vj[i];
+    wv.x -= h * pv.x;
+    wv.y -= h * pv.y;
+    w[i] = wv;
+    acc += wv.x * wv.x + wv.y * wv.y;
+  }
+  const double part = block_sum(acc, sh);
+  if (arrive_last(part, partials, counter)) {
+    const double s = final_sum(partials, counter, sh);
+    if (threadIdx.x == 0) {
+      const int ld = kMaxM + 1;
+      double* Hc = gs->H + (size_t)j * ld;
+      const double hnext = sqrt(s);
+      Hc[j + 1] = hnext;
+      for (int i = 0; i < j; ++i) {  // previous rotations
+        const double t = gs->cs[i] * Hc[i] + gs->sn[i] * Hc[i + 1];
+        Hc[i + 1] = -gs->sn[i] * Hc[i] + gs->cs[i] * Hc[i + 1];
+        Hc[i] = t;
+      }
+      const double rr = hypot(Hc[j], Hc[j + 1]);
+      const double c = Hc[j] / rr, sn = Hc[j + 1] / rr;
+      gs->cs[j] = c;
+      gs->sn[j] = sn;
+      Hc[j] = rr;
+      Hc[j + 1] = 0.0;
+      gs->g[j + 1] = -sn * gs->g[j];
+      gs->g[j] = c * gs->g[j];
+      const double rel = fabs(gs->g[j + 1]) / gs->ref;
+      gs->relres = rel;
+      gs->inv_h = (hnext > 0.0) ? 1.0 / hnext : 0.0;
+      int done = 0;
+      if (!isfinite(rel) || !isfinite(hnext)) done = 3;
+      else if (rel < gs->tol) done = 1;
+      else if (hnext == 0.0) done = 2;
+      gs->done = done;
+    }
+  }
+}
+
+// beta = ||x||, 1/beta, g = beta e_1; clears the column state of a new cycle.
+__global__ void __launch_bounds__(kRedThreads) k_norm(const double2* __restrict__ x, GmresState* gs, long long N,
+                                                      double* partials, unsigned* counter) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = x[i];
+    acc += v.x * v.x + v.y * v.y;
+  }
+  const double part = block_sum(acc, sh);
+  if (arrive_last(part, partials, counter)) {
+    const double s = final_sum(partials, counter, sh);
+    if (threadIdx.x == 0) {
+      const double b = sqrt(s);
+      gs->beta = b;
+      gs->inv_beta = (b > 0.0) ? 1.0 / b : 0.0;
+      gs->g[0] = b;
+      for (int i = 1; i <= kMaxM; ++i) gs->g[i] = 0.0;
+      gs->done = isfinite(b) ? 0 : 3;
+    }
+  }
+}
+
+__global__ void k_start_cycle(GmresState* gs, double ref, double tol) {
+  gs->ref = (ref > 0.0) ? ref : gs->beta;
+  gs->tol = tol;
+  gs->relres = gs->beta / gs->ref;
+}
+
+// y = R^{-1} g on the leading k x k triangle (single thread; k <= 64).
+__global__ void k_backsolve(GmresState* gs, int k) {
+  const int ld = kMaxM + 1;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = gs->g[i];
+    for (int jj = i + 1; jj < k; ++jj) s -= gs->H[(size_t)jj * ld + i] * gs->y[jj];
+    gs->y[i] = s / gs->H[(size_t)i * ld + i];
+  }
+}
+
+// out = sum_{i<k} y_i V_i
+__global__ void k_combine(const double2* __restrict__ V, long long ldv, const GmresState* gs, int k,
+                          double2* __restrict__ out, long long N) {
+  __shared__ double y[kMaxM];
+  if (threadIdx.x < k) y[threadIdx.x] = gs->y[threadIdx.x];
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    double2 a = make_double2(0.0, 0.0);
+    for (int q = 0; q < k; ++q) {
+      const double2 v = V[(size_t)q * ldv + i];
+      a.x += y[q] * v.x;
+      a.y += y[q] * v.y;
+    }
+    out[i] = a;
+  }
+}
+
+// x += sum_{i<k} y_i Z_i  (Z in FP32, accumulation in FP64)
+__global__ void k_combine_f32_add(const float2* __restrict__ Z, long long ldz, const GmresState* gs, int k,
+                                  double2* __restrict__ x, long long N) {
+  __shared__ double y[kMaxM];
+  if (threadIdx.x < k) y[threadIdx.x] = gs->y[threadIdx.x];
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    double2 a = x[i];
+    for (int q = 0; q < k; ++q) {
+      const float2 v = Z[(size_t)q * ldz + i];
+      a.x += y[q] * (double)v.x;
+      a.y += y[q] * (double)v.y;
+    }
+    x[i] = a;
+  }
+}
+
+// D = rho dt |u|^2, or rho dt |(u + u2)/2|^2 when u2 is given.
+__global__ void k_diag(const double2* __restrict__ u, const double2* __restrict__ u2, double* __restrict__ D,
+                       double rho_dt, long long N) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    double2 v = u[i];
+    if (u2) {
+      const double2 b = u2[i];
+      v.x = 0.5 * (v.x + b.x);
+      v.y = 0.5 * (v.y + b.y);
+    }
+    D[i] = rho_dt * (v.x * v.x + v.y * v.y);
+  }
+}
+
+// f = -i b
+__global__ void k_neg_i(const double2* __restrict__ b, double2* __restrict__ f, long long N) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = b[i];
+    f[i] = make_double2(v.y, -v.x);
+  }
+}
+
+__global__ void k_zero(double2* __restrict__ x, long long N) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    x[i] = make_double2(0.0, 0.0);
+}
+
+static inline unsigned ew_blocks(long long N) {
+  long long b = (N + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+void launch_dot_axpy(const double2* vi, double2* w, const double2* vprev, const double* hprev, double* out,
+                     long long N, int blocks, double* partials, unsigned* counter, cudaStream_t s) {
+  k_dot_axpy<<<blocks, kRedThreads, 0, s>>>(vi, w, vprev, hprev, out, N, partials, counter);
+}
+void launch_norm_givens(const double2* vj, double2* w, const double* hjj, GmresState* gs, int j, long long N,
+                        int blocks, double* partials, unsigned* counter, cudaStream_t s) {
+  k_norm_givens<<<blocks, kRedThreads, 0, s>>>(vj, w, hjj, gs, j, N, partials, counter);
+}
+void launch_norm(const double2* x, GmresState* gs, long long N, int blocks, double* partials, unsigned* counter,
+                 cudaStream_t s) {
+  k_norm<<<blocks, kRedThreads, 0, s>>>(x, gs, N, partials, counter);
+}
+void launch_start_cycle(GmresState* gs, double ref, double tol, cudaStream_t s) {
+  k_start_cycle<<<1, 1, 0, s>>>(gs, ref, tol);
+}
+void launch_backsolve(GmresState* gs, int k, cudaStream_t s) { k_backsolve<<<1, 1, 0, s>>>(gs, k); }
+void launch_combine(const double2* V, long long ldv, const GmresState* gs, int k, double2* out, long long N,
+                    cudaStream_t s) {
+  k_combine<<<ew_blocks(N), 256, 0, s>>>(V, ldv, gs, k, out, N);
+}
+void launch_combine_f32_add(const float2* Z, long long ldz, const GmresState* gs, int k, double2* x, long long N,
+                            cudaStream_t s) {
+  k_combine_f32_add<<<ew_blocks(N), 256, 0, s>>>(Z, ldz, gs, k, x, N);
+}
+void launch_diag(const double2* u, const double2* u2, double* D, double rho_dt, long long N, cudaStream_t s) {
+  k_diag<<<ew_blocks(N), 256, 0, s>>>(u, u2, D, rho_dt, N);
+}
+void launch_neg_i(const double2* b, double2* f, long long N, cudaStream_t s) {
+  k_neg_i<<<ew_blocks(N), 256, 0, s>>>(b, f, N);
+}
+void launch_zero(double2* x, long long N, cudaStream_t s) { k_zero<<<ew_blocks(N), 256, 0, s>>>(x, N); }
+
+}  // namespace rfnse

@@ -1,0 +1,362 @@
+// Solver drivers: the preconditioner and matrix sequences of line passes, right-preconditioned
+// GMRES (FP64), the mixed-precision FGMRES with FP64 iterative refinement, and the time steps.
+#include <cmath>
+#include "internal.cuh"
+#include "passes.cuh"
+#include "solve.cuh"
+
+namespace rfnse {
+
+static const double2 kOne = {1.0, 0.0};
+static const double2 kI = {0.0, 1.0};
+static const double2 kMinusOne = {-1.0, 0.0};
+static const double2 kMinusI = {0.0, -1.0};
+
+PassParams base_params(const rfnse_ctx* c, int axis, int half, bool fp32) {
+  PassParams p{};
+  const double hf = half ? 0.5 : 1.0;
+  p.d = c->d;
+  p.axis = axis;
+  for (int a = 0; a < 3; ++a) {
+    p.n_ax[a] = (a < c->d) ? c->n[a] : 1;
+    p.lam[a] = (a < c->d) ? c->lam[a] : nullptr;
+    p.mu[a] = (a < c->d) ? c->mu[a] * hf : 0.0;
+  }
+  p.n = c->n[axis];
+  p.L = c->L[axis];
+  p.log2L = c->log2L[axis];
+  p.stride = c->stride[axis];
+  p.nlines = c->N / c->n[axis];
+  p.tw = fp32 ? (const void*)c->tw32[axis] : (const void*)c->tw64[axis];
+  p.circ = c->circ[axis];
+  p.omega = c->p.omega;
+  p.toep_scale = p.mu[axis] / (double)p.L;
+  p.dst_scale = 1.0 / std::sqrt((double)p.L);
+  p.ca = kOne;
+  p.cb = kI;
+  return p;
+}
+
+// ---------------------------------------------------------------------------------------------
+// z = F~^{-1} v (eq. 'taupre'), optionally followed by w = add + a z + b (T - D) z.
+//   R    compute precision of the transforms
+//   TIN  storage of v (double2 when INSC: v is scaled by *in_scale and copied to copy_v)
+//   TMP  storage of the intermediate vectors t1, t2
+//   TZ   storage of z
+template <typename R, typename TIN, typename TMP, typename TZ, bool INSC, bool MATVEC>
+cudaError_t run_precon(rfnse_ctx* c, const TIN* v, const double* in_scale, double2* copy_v, TZ* z, int z_add,
+                       const double* D, double2* w, const double2* w_add, double2 a, double2 b, int half, TMP* t1,
+                       TMP* t2) {
+  constexpr bool F32 = sizeof(R) == 4;
+  cudaStream_t s = c->stream;
+  cudaError_t e;
+  constexpr int IS = INSC ? F_INSCALE : 0;
+  constexpr int TX = MATVEC ? F_TOEP_X : 0;
+  if (c->d == 1) {
+    PassParams p = base_params(c, 0, half, F32);
+    p.in = v; p.in_scale = in_scale; p.copy_out = copy_v; p.out = z; p.z_add = z_add; p.D = D;
+    p.acc_in = w_add; p.acc_out = w; p.ca = a; p.cb = b;
+    return launch_pass<R, TIN, TZ, IS | F_DST | F_LAM | F_DSCALE | TX>(p, s);
+  }
+  // first axis: forward DST (and the Arnoldi normalisation)
+  {
+    PassParams p = base_params(c, 0, half, F32);
+    p.in = v; p.in_scale = in_scale; p.copy_out = copy_v; p.out = t1;
+    if ((e = launch_pass<R, TIN, TMP, IS | F_DST>(p, s)) != cudaSuccess) return e;
+  }
+  TMP* cur = t1;
+  TMP* nxt = t2;
+  for (int a2 = 1; a2 < c->d - 1; ++a2) {  // middle axes (d = 3): forward DST
+    PassParams p = base_params(c, a2, half, F32);
+    p.in = cur; p.out = nxt;
+    if ((e = launch_pass<R, TMP, TMP, F_DST>(p, s)) != cudaSuccess) return e;
+    TMP* t = cur; cur = nxt; nxt = t;
+  }
+  {  // last axis: DST, divide by (w + i Lambda), DST
+    PassParams p = base_params(c, c->d - 1, half, F32);
+    p.in = cur; p.out = nxt;
+    if ((e = launch_pass<R, TMP, TMP, F_DST | F_LAM>(p, s)) != cudaSuccess) return e;
+    TMP* t = cur; cur = nxt; nxt = t;
+  }
+  for (int a2 = c->d - 2; a2 >= 1; --a2) {  // middle axes: inverse DST (S is involutory)
+    PassParams p = base_params(c, a2, half, F32);
+    p.in = cur; p.out = nxt;
+    if ((e = launch_pass<R, TMP, TMP, F_DST>(p, s)) != cudaSuccess) return e;
+    TMP* t = cur; cur = nxt; nxt = t;
+  }
+  {  // first axis: inverse DST, (wI + D)^{-1} sub-solve, optional Toeplitz along x
+    PassParams p = base_params(c, 0, half, F32);
+    p.in = cur; p.out = z; p.z_add = z_add; p.D = D;
+    p.acc_in = w_add; p.acc_out = w; p.ca = a; p.cb = b;
+    if ((e = launch_pass<R, TMP, TZ, F_DST | F_DSCALE | TX>(p, s)) != cudaSuccess) return e;
+  }
+  if (MATVEC) {
+    for (int a2 = 1; a2 < c->d; ++a2) {
+      PassParams p = base_params(c, a2, half, F32);
+      p.in = z; p.acc_in = w; p.acc_out = w; p.cb = b;
+      if ((e = launch_pass<R, TZ, TZ, F_TOEP_ACC>(p, s)) != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+// w = add + a z + b (T - D) z in FP64 (the Toeplitz products by circulant embedding).
+cudaError_t run_matvec_fp64(rfnse_ctx* c, const double2* z, const double* D, double2* w, const double2* add,
+                            double2 a, double2 b, int half) {
+  cudaStream_t s = c->stream;
+  cudaError_t e;
+  {
+    PassParams p = base_params(c, 0, half, false);
+    p.in = z; p.D = D; p.acc_in = add; p.acc_out = w; p.ca = a; p.cb = b;
+    if ((e = launch_pass<double, double2, double2, F_TOEP_X>(p, s)) != cudaSuccess) return e;
+  }
+  for (int a2 = 1; a2 < c->d; ++a2) {
+    PassParams p = base_params(c, a2, half, false);
+    p.in = z; p.acc_in = w; p.acc_out = w; p.cb = b;
+    if ((e = launch_pass<double, double2, double2, F_TOEP_ACC>(p, s)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t run_dst(rfnse_ctx* c, int axis, const double2* in, double2* out, int precision) {
+  if (precision) {
+    PassParams p = base_params(c, axis, 0, true);
+    p.in = in; p.out = out;
+    return launch_pass<float, double2, double2, F_DST>(p, c->stream);
+  }
+  PassParams p = base_params(c, axis, 0, false);
+  p.in = in; p.out = out;
+  return launch_pass<double, double2, double2, F_DST>(p, c->stream);
+}
+
+cudaError_t run_toeplitz(rfnse_ctx* c, int axis, const double2* in, double2* out, int half) {
+  PassParams p = base_params(c, axis, half, false);
+  p.in = in; p.acc_in = nullptr; p.acc_out = out; p.cb = kOne;
+  return launch_pass<double, double2, double2, F_TOEP_ACC>(p, c->stream);
+}
+
+cudaError_t run_apply_prec(rfnse_ctx* c, const double2* v, double2* z, const double* D, int half, int precision) {
+  if (precision) {
+    if (!c->t1f) return cudaErrorInvalidValue;
+    return run_precon<float, double2, float2, double2, false, false>(c, v, nullptr, nullptr, z, 0, D, nullptr,
+                                                                     nullptr, kOne, kI, half, c->t1f, c->t2f);
+  }
+  return run_precon<double, double2, double2, double2, false, false>(c, v, nullptr, nullptr, z, 0, D, nullptr,
+                                                                     nullptr, kOne, kI, half, c->t1, c->t2);
+}
+
+cudaError_t run_apply_A(rfnse_ctx* c, const double2* u, double2* out, const double* D, int half) {
+  // (D - T + iI) u = i u - (T - D) u
+  return run_matvec_fp64(c, u, D, out, nullptr, kI, kMinusOne, half);
+}
+
+// ---------------------------------------------------------------------------------------------
+static inline double* Hp(rfnse_ctx* c, int i, int j) { return &c->gs->H[(size_t)j * (kMaxM + 1) + i]; }
+
+static rfnse_status peek(rfnse_ctx* c, GmresPeek* out) {
+  RFNSE_CUDA_TRY(c, cudaMemcpyAsync(c->peek, c->gs, sizeof(GmresPeek), cudaMemcpyDeviceToHost, c->stream));
+  RFNSE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  *out = *c->peek;
+  return RFNSE_OK;
+}
+
+// Modified Gram-Schmidt of w against V_0..V_j, then h_{j+1,j}, Givens and the convergence test.
+static void arnoldi_orthogonalise(rfnse_ctx* c, int j) {
+  const long long N = c->N;
+  for (int i = 0; i <= j; ++i) {
+    launch_dot_axpy(c->V + (size_t)i * N, c->w, i > 0 ? c->V + (size_t)(i - 1) * N : nullptr,
+                    i > 0 ? Hp(c, i - 1, j) : nullptr, Hp(c, i, j), N, c->red_blocks, c->partials, c->counter,
+                    c->stream);
+  }
+  launch_norm_givens(c->V + (size_t)j * N, c->w, Hp(c, j, j), c->gs, j, N, c->red_blocks, c->partials, c->counter,
+                     c->stream);
+}
+
+// Right-preconditioned GMRES(m) for R x = f, x0 = 0 (paper Sec. 5 protocol), all FP64.
+static rfnse_status gmres_fp64(rfnse_ctx* c, const double* D, const double2* f, double2* x, int half, int* iters,
+                               double* relres) {
+  const long long N = c->N;
+  const int m = c->p.restart;
+  const double tol = c->p.tol;
+  GmresPeek pk;
+  launch_zero(x, N, c->stream);
+  launch_norm(f, c->gs, N, c->red_blocks, c->partials, c->counter, c->stream);
+  rfnse_status st = peek(c, &pk);
+  if (st) return st;
+  const double fnorm = pk.beta;
+  *iters = 0;
+  *relres = 0.0;
+  if (!std::isfinite(fnorm)) { c->err = "non-finite right-hand side"; return RFNSE_ENUMERIC; }
+  if (fnorm == 0.0) return RFNSE_OK;
+  launch_start_cycle(c->gs, fnorm, tol, c->stream);
+  const double2* r = f;
+  double beta = fnorm;
+  int it = 0;
+  for (;;) {
+    if (beta / fnorm < tol) { *relres = beta / fnorm; break; }
+    const double2* src = r;
+    const double* scale = &c->gs->inv_beta;
+    int k = 0;
+    int done = 0;
+    double rel = beta / fnorm;
+    for (int j = 0; j < m; ++j) {
+      RFNSE_CUDA_TRY(c, (run_precon<double, double2, double2, double2, true, true>(
+                            c, src, scale, c->V + (size_t)j * N, c->zb, 0, D, c->w, nullptr, kOne, kI, half, c->t1,
+                            c->t2)));
+      arnoldi_orthogonalise(c, j);
+      if ((st = peek(c, &pk))) return st;
+      ++it;
+      k = j + 1;
+      rel = pk.relres;
+      done = pk.done;
+      if (done == 3) { c->err = "non-finite value in the Arnoldi process"; return RFNSE_ENUMERIC; }
+      if (done || it >= c->p.max_it) break;
+      src = c->w;
+      scale = &c->gs->inv_h;
+    }
+    launch_backsolve(c->gs, k, c->stream);
+    launch_combine(c->V, N, c->gs, k, c->r, N, c->stream);
+    RFNSE_CUDA_TRY(c, (run_precon<double, double2, double2, double2, false, false>(
+                          c, c->r, nullptr, nullptr, x, 1, D, nullptr, nullptr, kOne, kI, half, c->t1, c->t2)));
+    *relres = rel;
+    if (done) break;
+    if (it >= c->p.max_it) {
+      *iters = it;
+      c->err = "GMRES reached max_it";
+      return RFNSE_ENOCONV;
+    }
+    // restart: true residual r = f - R x
+    RFNSE_CUDA_TRY(c, run_matvec_fp64(c, x, D, c->r, f, kMinusOne, kMinusI, half));
+    launch_norm(c->r, c->gs, N, c->red_blocks, c->partials, c->counter, c->stream);
+    if ((st = peek(c, &pk))) return st;
+    beta = pk.beta;
+    if (!std::isfinite(beta)) { c->err = "non-finite residual"; return RFNSE_ENUMERIC; }
+    launch_start_cycle(c->gs, fnorm, tol, c->stream);
+    r = c->r;
+    *relres = beta / fnorm;
+  }
+  *iters = it;
+  return RFNSE_OK;
+}
+
+// Mixed form: FP64 outer iterative refinement r = f - R x; each correction from an FGMRES inner solve
+// whose preconditioner and matrix products run in FP32 while the Arnoldi basis, Gram-Schmidt,
+// Givens and the solution update stay FP64.  Stops on the true FP64 relative residual.
+static rfnse_status solve_mixed(rfnse_ctx* c, const double* D, const double2* f, double2* x, int half, int* iters,
+                                double* relres, int* outer_out) {
+  const long long N = c->N;
+  const int m = c->p.restart;
+  const double tol = c->p.tol;
+  const double eta_min = c->p.inner_tol > 0 ? c->p.inner_tol : 1e-6;
+  const int max_outer = c->p.max_outer > 0 ? c->p.max_outer : 30;
+  GmresPeek pk;
+  launch_zero(x, N, c->stream);
+  launch_norm(f, c->gs, N, c->red_blocks, c->partials, c->counter, c->stream);
+  rfnse_status st = peek(c, &pk);
+  if (st) return st;
+  const double fnorm = pk.beta;
+  *iters = 0;
+  *relres = 0.0;
+  *outer_out = 0;
+  if (!std::isfinite(fnorm)) { c->err = "non-finite right-hand side"; return RFNSE_ENUMERIC; }
+  if (fnorm == 0.0) return RFNSE_OK;
+  const double2* r = f;
+  double beta = fnorm;
+  int it = 0, outer = 0;
+  for (;;) {
+    *relres = beta / fnorm;
+    if (beta / fnorm < tol) break;
+    if (outer >= max_outer || it >= c->p.max_it) {
+      *iters = it;
+      *outer_out = outer;
+      c->err = "mixed-precision refinement did not reach tol";
+      return RFNSE_ENOCONV;
+    }
+    const double eta = std::max(eta_min, 0.1 * tol * fnorm / beta);
+    launch_start_cycle(c->gs, beta, eta, c->stream);
+    const double2* src = r;
+    const double* scale = &c->gs->inv_beta;
+    int k = 0;
+    for (int j = 0; j < m && it < c->p.max_it; ++j) {
+      RFNSE_CUDA_TRY(c, (run_precon<float, double2, float2, float2, true, true>(
+                            c, src, scale, c->V + (size_t)j * N, c->Z32 + (size_t)j * N, 0, D, c->w, nullptr, kOne,
+                            kI, half, c->t1f, c->t2f)));
+      arnoldi_orthogonalise(c, j);
+      if ((st = peek(c, &pk))) return st;
+      ++it;
+      k = j + 1;
+      if (pk.done == 3) { c->err = "non-finite value in the Arnoldi process"; return RFNSE_ENUMERIC; }
+      if (pk.done) break;
+      src = c->w;
+      scale = &c->gs->inv_h;
+    }
+    launch_backsolve(c->gs, k, c->stream);
+    launch_combine_f32_add(c->Z32, N, c->gs, k, x, N, c->stream);
+    ++outer;
+    RFNSE_CUDA_TRY(c, run_matvec_fp64(c, x, D, c->r, f, kMinusOne, kMinusI, half));
+    launch_norm(c->r, c->gs, N, c->red_blocks, c->partials, c->counter, c->stream);
+    if ((st = peek(c, &pk))) return st;
+    beta = pk.beta;
+    if (!std::isfinite(beta)) { c->err = "non-finite residual"; return RFNSE_ENUMERIC; }
+    r = c->r;
+  }
+  *iters = it;
+  *outer_out = outer;
+  return RFNSE_OK;
+}
+
+rfnse_status solve_block(rfnse_ctx* c, const double* D, const double2* f, double2* x, int half, int* iters,
+                         double* relres) {
+  int outer = 0;
+  rfnse_status st;
+  if (c->p.precision == 1) {
+    st = solve_mixed(c, D, f, x, half, iters, relres, &outer);
+  } else {
+    st = gmres_fp64(c, D, f, x, half, iters, relres);
+    outer = 1;
+  }
+  c->last_outer = outer;
+  return st;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Time steps (paper Sec. 2.1/2.2): (D - T + iI) u^{n+1} = (T - D + iI) u^{n-1}, solved in the
+// block form R x = f with f = -i b = u^{n-1} - i (T - D) u^{n-1}.
+rfnse_status time_step(rfnse_ctx* c, int* iters, double* relres) {
+  const long long N = c->N;
+  const int inext = 3 - c->iprev - c->icur;
+  double2* un = c->u[inext];
+  rfnse_status st = RFNSE_OK, st2;
+  int it = 0;
+  if (c->step == 0) {
+    const double2* u0 = c->u[c->icur];
+    const double rdt = c->p.rho * c->p.dt * 0.5;
+    launch_diag(u0, nullptr, c->D, rdt, N, c->stream);
+    RFNSE_CUDA_TRY(c, run_matvec_fp64(c, u0, c->D, c->f, nullptr, kOne, kMinusI, 1));
+    st = solve_block(c, c->D, c->f, un, 1, &it, relres);
+    if (st != RFNSE_OK && st != RFNSE_ENOCONV) return st;
+    if (c->p.first_step == 1) {
+      int it2 = 0;
+      launch_diag(u0, un, c->D, rdt, N, c->stream);
+      RFNSE_CUDA_TRY(c, run_matvec_fp64(c, u0, c->D, c->f, nullptr, kOne, kMinusI, 1));
+      st2 = solve_block(c, c->D, c->f, un, 1, &it2, relres);
+      if (st2 != RFNSE_OK && st2 != RFNSE_ENOCONV) return st2;
+      if (st2 != RFNSE_OK) st = st2;
+      it += it2;
+    }
+  } else {
+    const double2* up = c->u[c->iprev];
+    const double2* uc = c->u[c->icur];
+    launch_diag(uc, nullptr, c->D, c->p.rho * c->p.dt, N, c->stream);
+    RFNSE_CUDA_TRY(c, run_matvec_fp64(c, up, c->D, c->f, nullptr, kOne, kMinusI, 0));
+    st = solve_block(c, c->D, c->f, un, 0, &it, relres);
+    if (st != RFNSE_OK && st != RFNSE_ENOCONV) return st;
+  }
+  c->iprev = c->icur;
+  c->icur = inext;
+  c->step += 1;
+  *iters = it;
+  return st;
+}
+
+}  // namespace rfnse

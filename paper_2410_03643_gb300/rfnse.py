@@ -1,0 +1,248 @@
+"""ctypes binding of the C ABI in include/rfnse.h.
+
+Argument marshalling only: every step of the solver runs in librfnse.so.  Device buffers are torch
+tensors (complex128 / float64 on a CUDA device), passed by data_ptr(); host buffers are numpy arrays.
+The library must have been built (paper_2410_03643_gb300.build.build_library, or
+__graft_entry__.build()); importing this module never falls back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+RFNSE_OK, RFNSE_EINVAL, RFNSE_ENOMEM, RFNSE_ECUDA, RFNSE_ENOCONV, RFNSE_ENUMERIC, RFNSE_ETIMEOUT = range(7)
+_STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENUMERIC", 6: "ETIMEOUT"}
+
+
+class RfnseError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"rfnse {_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class NoConvergence(RfnseError):
+    pass
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int),
+        ("n", ctypes.c_int * 3),
+        ("lo", ctypes.c_double * 3),
+        ("hi", ctypes.c_double * 3),
+        ("alpha", ctypes.c_double),
+        ("rho", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("omega", ctypes.c_double),
+        ("restart", ctypes.c_int),
+        ("max_it", ctypes.c_int),
+        ("tol", ctypes.c_double),
+        ("precision", ctypes.c_int),
+        ("first_step", ctypes.c_int),
+        ("inner_tol", ctypes.c_double),
+        ("max_outer", ctypes.c_int),
+    ]
+
+
+EXPORTED = ("rfnse_default_params", "rfnse_create", "rfnse_destroy", "rfnse_last_error", "rfnse_size",
+            "rfnse_set_state", "rfnse_get_state", "rfnse_run", "rfnse_apply_A", "rfnse_apply_prec",
+            "rfnse_dst", "rfnse_toeplitz", "rfnse_solve", "rfnse_get_coefficients")
+
+_lib = None
+
+
+def load_library(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load librfnse.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    path = path or _build.library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2410_03643_gb300.build.build_library()")
+    lib = ctypes.CDLL(path)
+    vp, cp, ip, dp = ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+    lib.rfnse_default_params.argtypes = [ctypes.POINTER(Params)]
+    lib.rfnse_default_params.restype = None
+    lib.rfnse_create.argtypes = [ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]
+    lib.rfnse_create.restype = ip
+    lib.rfnse_destroy.argtypes = [vp]
+    lib.rfnse_destroy.restype = None
+    lib.rfnse_last_error.argtypes = [vp]
+    lib.rfnse_last_error.restype = cp
+    lib.rfnse_size.argtypes = [vp]
+    lib.rfnse_size.restype = ctypes.c_longlong
+    lib.rfnse_set_state.argtypes = [vp, vp, vp, ip, ip]
+    lib.rfnse_set_state.restype = ip
+    lib.rfnse_get_state.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int), ip]
+    lib.rfnse_get_state.restype = ip
+    lib.rfnse_run.argtypes = [vp, ip, vp, ctypes.POINTER(ctypes.c_int), dp, ip]
+    lib.rfnse_run.restype = ip
+    lib.rfnse_apply_A.argtypes = [vp, vp, vp, vp, ip]
+    lib.rfnse_apply_A.restype = ip
+    lib.rfnse_apply_prec.argtypes = [vp, vp, vp, vp, ip, ip]
+    lib.rfnse_apply_prec.restype = ip
+    lib.rfnse_dst.argtypes = [vp, ip, vp, vp, ip]
+    lib.rfnse_dst.restype = ip
+    lib.rfnse_toeplitz.argtypes = [vp, ip, vp, vp, ip]
+    lib.rfnse_toeplitz.restype = ip
+    lib.rfnse_solve.argtypes = [vp, vp, vp, vp, ip, ctypes.POINTER(ctypes.c_int), dp]
+    lib.rfnse_solve.restype = ip
+    lib.rfnse_get_coefficients.argtypes = [vp, dp, dp]
+    lib.rfnse_get_coefficients.restype = ip
+    if path == _build.library_path():
+        _lib = lib
+    return lib
+
+
+def make_params(problem, precision: int = 0, inner_tol: float = 1e-6, max_outer: int = 30) -> Params:
+    """Params from a workloads.Problem."""
+    p = Params()
+    p.d = problem.d
+    for a in range(3):
+        p.n[a] = problem.n[a] if a < problem.d else 1
+        p.lo[a] = problem.lo[a] if a < problem.d else 0.0
+        p.hi[a] = problem.hi[a] if a < problem.d else 1.0
+    p.alpha = problem.alpha
+    p.rho = problem.rho
+    p.dt = problem.dt
+    p.omega = problem.omega
+    p.restart = problem.restart
+    p.max_it = problem.max_it
+    p.tol = problem.tol
+    p.precision = precision
+    p.first_step = problem.first_step
+    p.inner_tol = inner_tol
+    p.max_outer = max_outer
+    return p
+
+
+def _ptr(t) -> int:
+    return int(t.data_ptr())
+
+
+class Solver:
+    """One solver context (rfnse_create).  `stream` is a torch.cuda.Stream or None (current)."""
+
+    def __init__(self, problem, precision: int = 0, stream=None, inner_tol: float = 1e-6, max_outer: int = 30):
+        import torch
+        self.lib = load_library()
+        self.problem = problem
+        self.precision = precision
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.params = make_params(problem, precision, inner_tol, max_outer)
+        h = ctypes.c_void_p()
+        st = self.lib.rfnse_create(ctypes.byref(self.params), ctypes.c_void_p(self.stream.cuda_stream),
+                                   ctypes.byref(h))
+        if st != RFNSE_OK:
+            raise RfnseError(st, self.lib.rfnse_last_error(None).decode())
+        self.h = h
+        self.N = int(self.lib.rfnse_size(self.h))
+        self.shape = tuple(reversed(problem.n))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rfnse_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st == RFNSE_OK:
+            return
+        msg = self.lib.rfnse_last_error(self.h).decode()
+        if st == RFNSE_ENOCONV:
+            raise NoConvergence(st, msg)
+        raise RfnseError(st, msg)
+
+    # -- state and stepping ------------------------------------------------------------------
+    def set_state(self, u_cur, u_prev=None, step: int = 0):
+        """u_cur / u_prev: torch complex128 CUDA tensors of N values."""
+        self._check(self.lib.rfnse_set_state(self.h, _ptr(u_prev) if u_prev is not None else None,
+                                             _ptr(u_cur), step, 1))
+
+    def set_state_host(self, u_cur: np.ndarray, u_prev: Optional[np.ndarray] = None, step: int = 0):
+        uc = np.ascontiguousarray(u_cur, dtype=np.complex128)
+        up = np.ascontiguousarray(u_prev, dtype=np.complex128) if u_prev is not None else None
+        self._check(self.lib.rfnse_set_state(self.h, up.ctypes.data if up is not None else None,
+                                             uc.ctypes.data, step, 0))
+
+    def get_state(self):
+        import torch
+        up = torch.empty(self.N, dtype=torch.complex128, device="cuda")
+        uc = torch.empty(self.N, dtype=torch.complex128, device="cuda")
+        step = ctypes.c_int()
+        self._check(self.lib.rfnse_get_state(self.h, _ptr(up), _ptr(uc), ctypes.byref(step), 1))
+        return up, uc, step.value
+
+    def run(self, nsteps: int, traj=None, allow_noconv: bool = False) -> Tuple[np.ndarray, np.ndarray]:
+        """Advance nsteps; traj: optional torch complex128 CUDA tensor of nsteps*N values."""
+        iters = np.zeros(max(nsteps, 1), dtype=np.int32)
+        relres = np.zeros(max(nsteps, 1), dtype=np.float64)
+        st = self.lib.rfnse_run(self.h, nsteps, _ptr(traj) if traj is not None else None,
+                                iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                relres.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1)
+        if not (allow_noconv and st == RFNSE_ENOCONV):
+            self._check(st)
+        return iters[:nsteps], relres[:nsteps]
+
+    def run_host(self, nsteps: int, traj: Optional[np.ndarray] = None):
+        """Same as run with a host (numpy complex128) trajectory buffer."""
+        iters = np.zeros(max(nsteps, 1), dtype=np.int32)
+        relres = np.zeros(max(nsteps, 1), dtype=np.float64)
+        st = self.lib.rfnse_run(self.h, nsteps, traj.ctypes.data if traj is not None else None,
+                                iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                relres.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0)
+        self._check(st)
+        return iters[:nsteps], relres[:nsteps]
+
+    # -- building blocks ---------------------------------------------------------------------
+    def apply_A(self, u, D, half: bool = False):
+        import torch
+        out = torch.empty_like(u)
+        self._check(self.lib.rfnse_apply_A(self.h, _ptr(u), _ptr(out), _ptr(D), int(half)))
+        return out
+
+    def apply_prec(self, v, D, half: bool = False, precision: int = 0):
+        import torch
+        out = torch.empty_like(v)
+        self._check(self.lib.rfnse_apply_prec(self.h, _ptr(v), _ptr(out), _ptr(D), int(half), precision))
+        return out
+
+    def dst(self, axis: int, x, precision: int = 0):
+        import torch
+        out = torch.empty_like(x)
+        self._check(self.lib.rfnse_dst(self.h, axis, _ptr(x), _ptr(out), precision))
+        return out
+
+    def toeplitz(self, axis: int, x, half: bool = False):
+        import torch
+        out = torch.empty_like(x)
+        self._check(self.lib.rfnse_toeplitz(self.h, axis, _ptr(x), _ptr(out), int(half)))
+        return out
+
+    def solve(self, D, b, half: bool = False):
+        """u with (D - T + iI) u = b; returns (u, iters, relres)."""
+        import torch
+        u = torch.empty_like(b)
+        it = ctypes.c_int()
+        rr = ctypes.c_double()
+        self._check(self.lib.rfnse_solve(self.h, _ptr(D), _ptr(b), _ptr(u), int(half), ctypes.byref(it),
+                                         ctypes.byref(rr)))
+        return u, it.value, rr.value
+
+    def coefficients(self):
+        nmax = max(self.problem.n[: self.problem.d])
+        c = np.zeros(nmax)
+        lam = np.zeros(sum(self.problem.n[: self.problem.d]))
+        self._check(self.lib.rfnse_get_coefficients(self.h, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                    lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return c, lam

@@ -1,0 +1,258 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Element-by-element comparisons on the same seeded inputs: set-up tables, every building block
+(DST along each axis, Toeplitz along each axis, the system matrix, the preconditioner), single
+solves, and trajectories.  Tolerances: FP64 building blocks 1e-12 relative; FP32 transforms 2e-6;
+per-step solutions 1e-10 relative L2 (FP64 form) and 1e-8 (mixed form), GMRES iteration counts
+within +-1 of the oracle.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.fcd import fcd_coefficients
+from oracle.operators import ToeplitzOperator, apply_along_axis, diag_D, toeplitz_T0, block_R_apply
+from oracle.operators import complex_to_block, block_to_complex
+from oracle.precond import TauTBANPreconditioner
+from oracle.scheme import SchemeOracle
+from oracle.tau import dst_matrix, tau_eigenvalues
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2410_03643_gb300 import build
+    build.build_library()
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+
+
+def Solver(*a, **k):
+    from paper_2410_03643_gb300 import Solver as S
+    return S(*a, **k)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).ravel().copy()).to("cuda")
+
+
+def host(t, shape):
+    return t.detach().cpu().numpy().reshape(shape)
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(np.asarray(b).ravel()), 1e-300))
+
+
+SMALL = [
+    W.Problem(d=1, n=(255,), lo=(-20.0,), hi=(20.0,), alpha=1.5, rho=2.0, dt=0.01),
+    W.Problem(d=1, n=(7,), lo=(-2.0,), hi=(2.0,), alpha=1.9, rho=1.0, dt=0.05),
+    W.Problem(d=2, n=(63, 31), lo=(-6.0, -4.0), hi=(6.0, 5.0), alpha=1.7, rho=2.0, dt=0.01),
+    W.Problem(d=2, n=(15, 127), lo=(-3.0, -8.0), hi=(3.0, 8.0), alpha=1.2, rho=1.0, dt=0.02),
+    W.Problem(d=3, n=(15, 7, 31), lo=(-4.0, -3.0, -5.0), hi=(4.0, 3.0, 5.0), alpha=1.3, rho=1.0, dt=0.01),
+]
+IDS = ["1d255", "1d7", "2d63x31", "2d15x127", "3d15x7x31"]
+
+
+@pytest.mark.parametrize("p", SMALL, ids=IDS)
+def test_setup_tables_match_oracle(p):
+    s = Solver(p)
+    c, lam = s.coefficients()
+    c_ref = fcd_coefficients(p.alpha, max(p.n))
+    assert rel(c, c_ref) < 1e-13
+    off = 0
+    for a in range(p.d):
+        n = p.n[a]
+        assert rel(lam[off:off + n], tau_eigenvalues(c_ref, n)) < 1e-12
+        off += n
+
+
+@pytest.mark.parametrize("p", SMALL, ids=IDS)
+@pytest.mark.parametrize("precision", (0, 1))
+def test_dst_each_axis_matches_oracle(p, precision):
+    s = Solver(p)
+    x = W.random_field(p.shape, 21)
+    for a in range(p.d):
+        got = host(s.dst(a, dev(x), precision), p.shape)
+        want = apply_along_axis(dst_matrix(p.n[a]), x, a, p.d)
+        assert rel(got, want) < (1e-13 if precision == 0 else 2e-6), (a, rel(got, want))
+
+
+@pytest.mark.parametrize("p", SMALL, ids=IDS)
+@pytest.mark.parametrize("half", (False, True))
+def test_toeplitz_each_axis_matches_oracle(p, half):
+    s = Solver(p)
+    x = W.random_field(p.shape, 22)
+    c = fcd_coefficients(p.alpha, max(p.n))
+    for a in range(p.d):
+        mu = (0.5 if half else 1.0) * p.dt / p.h(a) ** p.alpha
+        got = host(s.toeplitz(a, dev(x), half), p.shape)
+        want = mu * apply_along_axis(toeplitz_T0(c, p.n[a]), x, a, p.d)
+        assert rel(got, want) < 1e-12, (a, rel(got, want))
+
+
+@pytest.mark.parametrize("p", SMALL, ids=IDS)
+def test_system_matrix_matches_oracle(p):
+    s = Solver(p)
+    u = W.random_field(p.shape, 23)
+    D = diag_D(W.random_field(p.shape, 24), p.rho, p.dt)
+    got = host(s.apply_A(dev(u), dev(D)), p.shape)
+    T = ToeplitzOperator(p)
+    want = D * u - T(u) + 1j * u
+    assert rel(got, want) < 1e-12
+    # the same operator through the real block form of the oracle: A u = i R u with u <-> [Im; Re]
+    Rx = block_to_complex(block_R_apply(complex_to_block(u), T, D))
+    assert rel(got, 1j * Rx) < 1e-12
+
+
+@pytest.mark.parametrize("p", SMALL, ids=IDS)
+@pytest.mark.parametrize("precision", (0, 1))
+@pytest.mark.parametrize("half", (False, True))
+def test_preconditioner_matches_oracle(p, precision, half):
+    s = Solver(p)
+    v = W.random_field(p.shape, 25)
+    D = diag_D(W.random_field(p.shape, 26), p.rho, p.dt)
+    got = host(s.apply_prec(dev(v), dev(D), half, precision), p.shape)
+    P = TauTBANPreconditioner(p, p.omega, 0.5 if half else 1.0)
+    want = block_to_complex(P.apply_inverse(complex_to_block(v), D))
+    assert rel(got, want) < (1e-12 if precision == 0 else 5e-6)
+
+
+@pytest.mark.parametrize("p", SMALL, ids=IDS)
+@pytest.mark.parametrize("precision", (0, 1))
+def test_single_solve_matches_oracle(p, precision):
+    p = p.replace(tol=1e-10)
+    s = Solver(p, precision=precision)
+    u_n = W.u0_sech_product(p, [1.0] * p.d)
+    D = diag_D(u_n, p.rho, p.dt)
+    b = W.random_field(p.shape, 27)
+    u, it, rr = s.solve(dev(D), dev(b))
+    o = SchemeOracle(p)
+    res = o.solve(o.T, o.P, D, b)
+    u_ref = block_to_complex(res.x)
+    got = host(u, p.shape)
+    if precision == 0:
+        assert rel(got, u_ref) < 1e-10
+        assert abs(it - res.iters) <= 1
+    else:
+        assert rel(got, u_ref) < 1e-8
+    assert rr < p.tol
+
+
+def _traj_case(p, nsteps, precision, u0):
+    s = Solver(p, precision=precision)
+    s.set_state(dev(u0))
+    traj = torch.empty(nsteps * p.size, dtype=torch.complex128, device="cuda")
+    iters, relres = s.run(nsteps, traj)
+    got = traj.cpu().numpy().reshape((nsteps,) + p.shape)
+    o = SchemeOracle(p)
+    ref, its_ref, _ = o.run(u0, nsteps)
+    return got, iters, ref, its_ref
+
+
+@pytest.mark.parametrize("p", SMALL, ids=IDS)
+@pytest.mark.parametrize("precision", (0, 1))
+def test_trajectory_matches_oracle(p, precision):
+    p = p.replace(tol=1e-10)
+    u0 = W.u0_sech_product(p, [1.0] * p.d) if p.d > 1 else W.u0_sech_1d(p)
+    nsteps = 6
+    got, iters, ref, its_ref = _traj_case(p, nsteps, precision, u0)
+    tol = 1e-10 if precision == 0 else 1e-8
+    for k in range(nsteps):
+        assert rel(got[k], ref[k]) < tol, (k, rel(got[k], ref[k]))
+        if precision == 0:
+            assert abs(int(iters[k]) - its_ref[k]) <= 1, (k, iters, its_ref)
+
+
+def test_first_step_predictor_only_matches_oracle():
+    p = SMALL[2].replace(first_step=0, tol=1e-10)
+    u0 = W.u0_sech_product(p, [1.0, 1.0])
+    got, iters, ref, its_ref = _traj_case(p, 2, 0, u0)
+    for k in range(2):
+        assert rel(got[k], ref[k]) < 1e-10
+
+
+def test_restart_and_resume_state():
+    """Small restart length forces GMRES restarts; resuming from get_state reproduces the run."""
+    p = SMALL[2].replace(restart=2, tol=1e-10)
+    u0 = W.u0_sech_product(p, [1.0, 1.0])
+    got, iters, ref, its_ref = _traj_case(p, 4, 0, u0)
+    for k in range(4):
+        assert rel(got[k], ref[k]) < 1e-10
+        assert abs(int(iters[k]) - its_ref[k]) <= 1
+    s = Solver(p)
+    s.set_state(dev(u0))
+    s.run(2)
+    up, uc, step = s.get_state()
+    assert step == 2
+    s2 = Solver(p)
+    s2.set_state(uc, up, step)
+    s2.run(2)
+    _, uc2, _ = s2.get_state()
+    assert rel(host(uc2, p.shape), ref[3]) < 1e-10
+
+
+def test_alpha2_rho0_single_iteration():
+    p = SMALL[2].replace(alpha=2.0, rho=0.0, tol=1e-10)
+    s = Solver(p)
+    b = W.random_field(p.shape, 31)
+    D = np.zeros(p.shape)
+    _, it, _ = s.solve(dev(D), dev(b))
+    assert it == 1
+
+
+def test_zero_rhs_and_zero_steps():
+    p = SMALL[0]
+    s = Solver(p)
+    u, it, rr = s.solve(dev(np.zeros(p.shape)), dev(np.zeros(p.shape, complex)))
+    assert it == 0 and rr == 0.0 and not torch.any(u != 0)
+    s.set_state(dev(W.u0_sech_1d(p)))
+    iters, _ = s.run(0)
+    assert len(iters) == 0
+
+
+def test_max_it_reports_noconvergence():
+    from paper_2410_03643_gb300 import NoConvergence
+    p = SMALL[2].replace(max_it=1, tol=1e-14)
+    s = Solver(p)
+    b = W.random_field(p.shape, 32)
+    D = diag_D(W.random_field(p.shape, 33), p.rho, p.dt)
+    with pytest.raises(NoConvergence):
+        s.solve(dev(D), dev(b))
+
+
+def test_mass_conserved_on_gpu():
+    p = SMALL[2].replace(tol=1e-13)
+    s = Solver(p)
+    u0 = W.u0_sech_product(p, [1.0, 1.0])
+    s.set_state(dev(u0))
+    traj = torch.empty(8 * p.size, dtype=torch.complex128, device="cuda")
+    s.run(8, traj)
+    seq = [u0] + list(traj.cpu().numpy().reshape((8,) + p.shape))
+    for k in range(1, 8):
+        assert abs(np.linalg.norm(seq[k + 1]) - np.linalg.norm(seq[k - 1])) < 1e-11 * np.linalg.norm(u0)
+
+
+# --- the workloads at their full sizes --------------------------------------------------------
+
+def test_config_1d_full_trajectory_fp64():
+    """d=1, n=1023, alpha=1.5, rho=2, dt=0.01, 50 steps, FP64, tol 1e-10: every step."""
+    p, u0, nsteps = W.config_1d()
+    got, iters, ref, its_ref = _traj_case(p, nsteps, 0, u0)
+    for k in range(nsteps):
+        assert rel(got[k], ref[k]) < 1e-10, k
+        assert abs(int(iters[k]) - its_ref[k]) <= 1
+
+
+@pytest.mark.parametrize("alpha", W.CONFIG_2D_ALPHAS)
+@pytest.mark.parametrize("precision", (0, 1))
+def test_config_2d_511_first_steps(alpha, precision):
+    """d=2, n=511^2, dt=0.005: the first three steps of the full-size workload against the oracle."""
+    p, u0, _ = W.config_2d(alpha)
+    got, iters, ref, its_ref = _traj_case(p, 3, precision, u0)
+    for k in range(3):
+        assert rel(got[k], ref[k]) < (1e-10 if precision == 0 else 1e-8), (k, rel(got[k], ref[k]))
+        if precision == 0:
+            assert abs(int(iters[k]) - its_ref[k]) <= 1
