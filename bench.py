@@ -1,0 +1,401 @@
+#!/usr/bin/env python3
+"""Benchmark: DOF x timesteps / s of the tau-preconditioned GMRES time stepper.
+
+Workload (default): d = 2, n = 511 x 511 on [-10,10]^2, rho = 2, dt = 0.005, u0 = sech(x)sech(y)e^{i(x+y)},
+alpha in {1.2, 1.5, 1.9} (three independent instances), tol 1e-10.  One bench step advances all three
+instances by one time step (a GMRES solve each) in the mixed form (FP32 transforms inside FGMRES,
+FP64 Arnoldi/Givens and FP64 outer residual); the plain FP64 form is timed the same way and reported
+beside it, with the difference between the two trajectories.  DOF = complex grid unknowns.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload 2d|3d|1d]
+
+Multi-GPU (torchrun): every rank advances its own copy of the three instances (independent problems,
+no collective on the data path; weak scaling); value = all ranks' DOF x steps / max rank time.
+--impl reference times the CPU oracle (test infrastructure) on the host cores, rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "DOF*timesteps/s"
+UNIT = "DOF*timesteps/s"
+FP64_ALU_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="2d", choices=["2d", "3d", "1d"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    return ap.parse_args()
+
+
+def workload(name):
+    """[(problem, u0)] and a description."""
+    if name == "2d":
+        inst = [W.config_2d(a)[:2] for a in W.CONFIG_2D_ALPHAS]
+        desc = {"workload": "2d_n511x511_alpha{1.2,1.5,1.9}_rho2_dt0.005_tol1e-10", "d": 2, "n": [511, 511],
+                "box": [-10, 10], "alphas": list(W.CONFIG_2D_ALPHAS), "instances": 3}
+    elif name == "3d":
+        p, u0, _ = W.config_3d()
+        inst = [(p, u0)]
+        desc = {"workload": "3d_n255^3_alpha1.7_rho1_dt0.01_tol1e-8", "d": 3, "n": [255, 255, 255],
+                "box": [-8, 8], "alphas": [1.7], "instances": 1}
+    else:
+        p, u0, _ = W.config_1d()
+        inst = [(p, u0)]
+        desc = {"workload": "1d_n1023_alpha1.5_rho2_dt0.01_tol1e-10", "d": 1, "n": [1023], "box": [-20, 20],
+                "alphas": [1.5], "instances": 1}
+    return inst, desc
+
+
+# --- clocks -------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms while active."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t_on = self.t_off = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark_on(self):
+        self.t_on = time.time()
+
+    def mark_off(self):
+        self.t_off = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [l for t, l in self.lines if self.t_on is not None and self.t_on - 0.05 <= t <= self.t_off + 0.05]
+        sm, smmax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            f = [x.strip() for x in r.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smmax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smmax) if smmax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --- distributed helpers ------------------------------------------------------------------------
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --- the CPU oracle as the baseline / reference arm ---------------------------------------------
+def oracle_sample(inst, nsteps: int):
+    """Time `nsteps` regular time steps (n >= 1) of the first instance with the CPU oracle.
+    Returns (DOF x steps / s, seconds, steps)."""
+    from oracle.scheme import SchemeOracle
+    p, u0 = inst[0]
+    o = SchemeOracle(p)
+    u1, _, _ = o.first_step(u0)
+    up, uc = u0, u1
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        un, _, _ = o.step(up, uc)
+        up, uc = uc, un
+    dt = time.perf_counter() - t0
+    return p.size * nsteps / dt, dt, nsteps
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    inst, desc = workload(args.workload)
+    from oracle.scheme import SchemeOracle
+    # one bench step = one time step of one instance (instances visited in turn), CPU oracle
+    states = []
+    for p, u0 in inst:
+        o = SchemeOracle(p)
+        u1, _, _ = o.first_step(u0)
+        states.append([o, u0, u1])
+    k = 0
+
+    def one():
+        nonlocal k
+        st = states[k % len(states)]
+        o, up, uc = st
+        un, _, _ = o.step(up, uc)
+        st[1], st[2] = uc, un
+        k += 1
+        return o.p.size
+
+    for _ in range(args.warmup):
+        one()
+    dof = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        dof += one()
+    dt = time.perf_counter() - t0
+    value = dof / dt
+    cores = host_cores()
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (closed-form initial data of the paper's shape)",
+           "config": dict(desc, sample="one time step of one alpha instance per bench step"),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{args.steps} time steps, instances in turn, numpy/BLAS on {cores} host cores"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# --- our CUDA path --------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2410_03643_gb300 import build, rfnse
+    build.build_library()
+    inst, desc = workload(args.workload)
+    stream = torch.cuda.current_stream()
+
+    def make(precision):
+        solvers = []
+        for p, u0 in inst:
+            s = rfnse.Solver(p, precision=precision, stream=stream)
+            s.set_state(torch.from_numpy(u0.ravel().copy()).to(dev))
+            solvers.append(s)
+        return solvers
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    dof_per_step = sum(p.size for p, _ in inst)
+
+    def timed(solvers, steps, warmup, profile_kind=0, clocks=None):
+        for _ in range(warmup):
+            for s in solvers:
+                s.run(1)
+        torch.cuda.synchronize()
+        if profile_kind:
+            for s in solvers:
+                s.profile(profile_kind)
+        launches0 = rfnse.launch_count()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        iters = []
+        barrier(world)
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.mark_on()
+        wall0 = time.perf_counter()
+        for k in range(steps):
+            flush.fill_(float(k))                       # evict L2 between timed steps
+            evs[k][0].record(stream)
+            for s in solvers:
+                it, _ = s.run(1)
+                iters.append(int(it[0]))
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        if clocks:
+            clocks.mark_off()
+        barrier(world)
+        launches = rfnse.launch_count() - launches0
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        prof = None
+        if profile_kind:
+            tot = [0, 0.0, 0.0, 0.0]
+            for s in solvers:
+                n, pms, fl, by = s.profile_read()
+                tot[0] += n; tot[1] += pms; tot[2] += fl; tot[3] += by
+                s.profile(0)
+            prof = tot
+        return ms, wall, launches, iters, prof
+
+    # headline: mixed form
+    mixed = make(1)
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    dom_kind = rfnse.K_TOEP_X if args.workload != "1d" else (rfnse.K_DST | rfnse.K_LAM | rfnse.K_DSCALE | rfnse.K_TOEP_X)
+    ms, wall, launches, iters_m, prof = timed(mixed, args.steps, args.warmup, profile_kind=dom_kind, clocks=clocks)
+    clk = clocks.stop() if clocks else None
+    ms_max = reduce_max(ms, world, dev)
+    value = world * dof_per_step * args.steps / (ms_max * 1e-3)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
+           "data": "synthetic (closed-form initial data of the paper's shape)",
+           "config": dict(desc, precision="mixed: FP32 transforms in FGMRES, FP64 Arnoldi/Givens/residual",
+                          l2="256 MiB buffer written between timed steps",
+                          parallelism=f"{world} GPU(s), instances replicated per GPU"),
+           "gpu_launches": launches,
+           "iters_per_solve_mean": float(np.mean(iters_m)) if iters_m else None}
+
+    # roofline of the dominant kernel class (FP64 Toeplitz pass along x of the outer residual)
+    if prof and prof[0] > 0:
+        n, pms, fl, by = prof
+        achieved = fl / (pms * 1e-3) / 1e12
+        peak = FP64_ALU_PEAK_FLOPS / 1e12
+        out["roofline"] = {"bound": "alu", "kernel": "k_line_pass<double,F_TOEP_X> (FP64 Toeplitz x-pass)",
+                           "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                           "traffic": None, "launches": n, "avg_launch_us": 1e3 * pms / n,
+                           "share_of_step_time": pms / ms if ms > 0 else None,
+                           "algorithmic_bytes_per_launch": by / n,
+                           "achieved_GBps": by / (pms * 1e-3) / 1e9,
+                           "peak_note": "FP64 FMA peak 152 SM x 2 FMA/clk x 2.07 GHz (derived; measured 1.19 TFLOP/s at 1.995 GHz)"}
+    if clk:
+        out["clocks"] = clk
+
+    # plain FP64 form, same protocol, and the distance between the two trajectories
+    if not args.no_fp64:
+        fp64 = make(0)
+        ms64, _, _, iters64, _ = timed(fp64, args.steps, args.warmup)
+        ms64 = reduce_max(ms64, world, dev)
+        errs = []
+        for a, b in zip(mixed, fp64):
+            _, ua, _ = a.get_state()
+            _, ub, _ = b.get_state()
+            errs.append(float(torch.linalg.vector_norm(ua - ub) / torch.linalg.vector_norm(ub)))
+        out["fp64"] = {"value": world * dof_per_step * args.steps / (ms64 * 1e-3), "ms_per_step": ms64 / args.steps,
+                       "iters_per_solve_mean": float(np.mean(iters64)) if iters64 else None}
+        out["mixed_vs_fp64_rel_l2_after_run"] = max(errs)
+        out["mixed_speedup_vs_fp64"] = ms64 / ms_max
+        for s in fp64:
+            s.close()
+
+    # end to end through the C ABI with host buffers: H2D of the step's inputs, D2H of its result
+    if not args.no_e2e:
+        e2e_solvers = make(1)
+        for s in e2e_solvers:
+            s.run(2)  # reach a regular step
+        hosts = []
+        for s in e2e_solvers:
+            up, uc, step = s.get_state()
+            pin_up = torch.empty(s.N, dtype=torch.complex128, pin_memory=True)
+            pin_uc = torch.empty(s.N, dtype=torch.complex128, pin_memory=True)
+            pin_out = torch.empty(s.N, dtype=torch.complex128, pin_memory=True)
+            pin_up.copy_(up.cpu())
+            pin_uc.copy_(uc.cpu())
+            hosts.append([pin_up, pin_uc, pin_out, step])
+        steps_e2e = max(1, min(args.steps, 30))
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(steps_e2e):
+            for s, h in zip(e2e_solvers, hosts):
+                s.set_state_host(h[1].numpy(), h[0].numpy(), h[3])
+                s.run_host(1, h[2].numpy())
+                h[0], h[1], h[2] = h[1], h[2], h[0]
+                h[3] += 1
+        torch.cuda.synchronize()
+        e2e_s = reduce_max(time.perf_counter() - t0, world, dev)
+        nb = sum(s.N for s in e2e_solvers) * 16
+        out["e2e"] = {"value": world * dof_per_step * steps_e2e / e2e_s, "unit": UNIT,
+                      "h2d_bytes_per_step": 2 * nb, "d2h_bytes_per_step": nb, "steps": steps_e2e}
+        for s in e2e_solvers:
+            s.close()
+
+    # the CPU oracle on the host cores (bounded sample), rank 0 at N = 1 only
+    if not args.no_cpu and rank == 0 and world == 1:
+        n_cpu = 30 if args.workload != "3d" else 1
+        v, secs, n = oracle_sample(inst, n_cpu)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                               "sample": f"{n} time steps of the alpha={inst[0][0].alpha} instance "
+                                         f"({secs:.1f} s), numpy/BLAS dense-transform oracle"}
+    for s in mixed:
+        s.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

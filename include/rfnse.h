@@ -140,6 +140,33 @@ int rfnse_solve(rfnse_ctx* ctx, const double* D, const void* b, void* u, int hal
    Either pointer may be NULL. */
 int rfnse_get_coefficients(rfnse_ctx* ctx, double* c, double* lam);
 
+/* ---- instrumentation -------------------------------------------------------------------------- */
+
+/* Number of CUDA kernels this library has launched in the calling process (all contexts). */
+long long rfnse_launch_count(void);
+
+/* Kernel classes of rfnse_profile: OR of the operations a line pass fuses, plus RFNSE_K_FP32 for
+   passes computing in FP32.  RFNSE_K_INSCALE is ignored when matching. */
+enum {
+  RFNSE_K_INSCALE = 1,   /* Arnoldi normalisation v = w / h folded into the load */
+  RFNSE_K_DST = 2,       /* DST-I along the axis */
+  RFNSE_K_LAM = 4,       /* divide by (omega + i Lambda) and DST-I again (last axis) */
+  RFNSE_K_DSCALE = 8,    /* (omega I + D) sub-solve of the preconditioner */
+  RFNSE_K_TOEP_X = 16,   /* Toeplitz product along x with the diagonal and block coupling */
+  RFNSE_K_TOEP_ACC = 32, /* Toeplitz product along y or z, accumulated */
+  RFNSE_K_FP32 = 256
+};
+
+/* Start timing every launch of kernel class `kind` (0 = off) issued by ctx: a CUDA event pair is
+   recorded around each such launch on the context's stream.  Resets the accumulated figures. */
+int rfnse_profile(rfnse_ctx* ctx, int kind);
+
+/* Synchronise the context's stream and report, since rfnse_profile: the number of launches of the
+   class, their summed device time in ms, and their summed algorithmic flops (5 L log2 L per complex
+   FFT of length L per grid line) and bytes (each operand read once, each result written once).
+   Any pointer may be NULL. */
+int rfnse_profile_read(rfnse_ctx* ctx, int* launches, double* ms, double* flops, double* bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -51,6 +51,7 @@ void free_ctx(rfnse_ctx* c) {
   cudaFree(c->counter);
   cudaFree(c->gs);
   if (c->peek) cudaFreeHost(c->peek);
+  for (cudaEvent_t ev : c->prof_events) cudaEventDestroy(ev);
   delete c;
 }
 
@@ -306,6 +307,34 @@ int rfnse_get_coefficients(rfnse_ctx* c, double* cc, double* lam) {
     }
   }
   RFNSE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return RFNSE_OK;
+}
+
+long long rfnse_launch_count(void) { return g_kernel_launches.load(); }
+
+int rfnse_profile(rfnse_ctx* c, int kind) {
+  if (!c || kind < 0) return RFNSE_EINVAL;
+  RFNSE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->prof_kind = kind;
+  c->prof_used = 0;
+  c->prof_flops = 0.0;
+  c->prof_bytes = 0.0;
+  return RFNSE_OK;
+}
+
+int rfnse_profile_read(rfnse_ctx* c, int* launches, double* ms, double* flops, double* bytes) {
+  if (!c) return RFNSE_EINVAL;
+  RFNSE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  double total = 0.0;
+  for (size_t i = 0; i + 1 < c->prof_used; i += 2) {
+    float t = 0.f;
+    RFNSE_CUDA_TRY(c, cudaEventElapsedTime(&t, c->prof_events[i], c->prof_events[i + 1]));
+    total += t;
+  }
+  if (launches) *launches = (int)(c->prof_used / 2);
+  if (ms) *ms = total;
+  if (flops) *flops = c->prof_flops;
+  if (bytes) *bytes = c->prof_bytes;
   return RFNSE_OK;
 }
 

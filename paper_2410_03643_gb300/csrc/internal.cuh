@@ -2,13 +2,19 @@
 // shared between translation units.
 #pragma once
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdio>
 #include <string>
+#include <vector>
 #include "../../include/rfnse.h"
 
 namespace rfnse {
 
 constexpr int kMaxM = 64;  // largest supported restart length
+
+// Number of kernels this library has launched in the process (all contexts).
+extern std::atomic<long long> g_kernel_launches;
+inline void count_launch(long long k = 1) { g_kernel_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // Device-resident Arnoldi / Givens state of one GMRES cycle.  H is stored by columns:
 // H(i, j) = H[j * (kMaxM + 1) + i].
@@ -99,6 +105,11 @@ struct rfnse_ctx {
   // per-step statistics of the last solve
   int last_iters = 0, last_outer = 0;
   double last_relres = 0.0;
+  // kernel-class profiling (rfnse_profile): CUDA events around every launch of one pass kind
+  int prof_kind = 0;
+  std::vector<cudaEvent_t> prof_events;  // pairs (start, stop)
+  size_t prof_used = 0;                  // events in use
+  double prof_flops = 0.0, prof_bytes = 0.0;
   std::string err;
 };
 

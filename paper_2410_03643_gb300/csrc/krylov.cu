@@ -7,6 +7,8 @@
 
 namespace rfnse {
 
+std::atomic<long long> g_kernel_launches{0};
+
 constexpr int kRedThreads = 256;
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -227,32 +229,40 @@ static inline unsigned ew_blocks(long long N) {
 
 void launch_dot_axpy(const double2* vi, double2* w, const double2* vprev, const double* hprev, double* out,
                      long long N, int blocks, double* partials, unsigned* counter, cudaStream_t s) {
+  count_launch();
   k_dot_axpy<<<blocks, kRedThreads, 0, s>>>(vi, w, vprev, hprev, out, N, partials, counter);
 }
 void launch_norm_givens(const double2* vj, double2* w, const double* hjj, GmresState* gs, int j, long long N,
                         int blocks, double* partials, unsigned* counter, cudaStream_t s) {
+  count_launch();
   k_norm_givens<<<blocks, kRedThreads, 0, s>>>(vj, w, hjj, gs, j, N, partials, counter);
 }
 void launch_norm(const double2* x, GmresState* gs, long long N, int blocks, double* partials, unsigned* counter,
                  cudaStream_t s) {
+  count_launch();
   k_norm<<<blocks, kRedThreads, 0, s>>>(x, gs, N, partials, counter);
 }
 void launch_start_cycle(GmresState* gs, double ref, double tol, cudaStream_t s) {
+  count_launch();
   k_start_cycle<<<1, 1, 0, s>>>(gs, ref, tol);
 }
 void launch_backsolve(GmresState* gs, int k, cudaStream_t s) { k_backsolve<<<1, 1, 0, s>>>(gs, k); }
 void launch_combine(const double2* V, long long ldv, const GmresState* gs, int k, double2* out, long long N,
                     cudaStream_t s) {
+  count_launch();
   k_combine<<<ew_blocks(N), 256, 0, s>>>(V, ldv, gs, k, out, N);
 }
 void launch_combine_f32_add(const float2* Z, long long ldz, const GmresState* gs, int k, double2* x, long long N,
                             cudaStream_t s) {
+  count_launch();
   k_combine_f32_add<<<ew_blocks(N), 256, 0, s>>>(Z, ldz, gs, k, x, N);
 }
 void launch_diag(const double2* u, const double2* u2, double* D, double rho_dt, long long N, cudaStream_t s) {
+  count_launch();
   k_diag<<<ew_blocks(N), 256, 0, s>>>(u, u2, D, rho_dt, N);
 }
 void launch_neg_i(const double2* b, double2* f, long long N, cudaStream_t s) {
+  count_launch();
   k_neg_i<<<ew_blocks(N), 256, 0, s>>>(b, f, N);
 }
 void launch_zero(double2* x, long long N, cudaStream_t s) { k_zero<<<ew_blocks(N), 256, 0, s>>>(x, N); }

@@ -26,6 +26,7 @@
 #include <cstdint>
 #include "cplx.cuh"
 #include "fft_line.cuh"
+#include "internal.cuh"
 
 namespace rfnse {
 
@@ -270,8 +271,25 @@ inline void pass_geometry(int L, long long nlines_or_stride, int& nt, int& B) {
   if (B < 1) B = 1;
 }
 
+// Algorithmic work of one launch: 5 L log2 L flops per complex FFT of length L per line, and
+// bytes with every operand read once and every result written once.
 template <typename R, typename TIN, typename TOUT, int FLAGS>
-cudaError_t launch_pass(PassParams p, cudaStream_t s) {
+void pass_work(const PassParams& p, double& flops, double& bytes) {
+  const double lines = (double)p.nlines, N = lines * p.n;
+  int nfft = 0;
+  if (FLAGS & F_DST) ++nfft;
+  if (FLAGS & F_LAM) ++nfft;
+  if (FLAGS & (F_TOEP_X | F_TOEP_ACC)) nfft += 2;
+  flops = lines * nfft * 5.0 * p.L * p.log2L;
+  bytes = N * sizeof(TIN);
+  if (FLAGS & F_INSCALE) bytes += N * sizeof(double2);
+  if ((FLAGS & F_DST) && p.out) bytes += N * sizeof(TOUT) * (p.z_add ? 2 : 1);
+  if (FLAGS & (F_DSCALE | F_TOEP_X)) bytes += N * sizeof(double);
+  if (FLAGS & (F_TOEP_X | F_TOEP_ACC)) bytes += N * sizeof(double2) * (p.acc_in ? 2 : 1);
+}
+
+template <typename R, typename TIN, typename TOUT, int FLAGS>
+cudaError_t launch_pass(rfnse_ctx* c, PassParams p, cudaStream_t s) {
   using V = cv<R>;
   const bool xax = (p.stride == 1);
   pass_geometry(p.L, xax ? p.nlines : p.stride, p.nt, p.B);
@@ -294,7 +312,30 @@ cudaError_t launch_pass(PassParams p, cudaStream_t s) {
     attr_set = true;
   }
   if (grid <= 0) return cudaSuccess;
+  const int kind = FLAGS | (sizeof(R) == 4 ? 256 : 0);
+  const bool prof = c->prof_kind != 0 && ((c->prof_kind | F_INSCALE) == (kind | F_INSCALE));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (prof) {
+    while (c->prof_used + 2 > c->prof_events.size()) {
+      cudaEvent_t ev;
+      cudaError_t e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) return e;
+      c->prof_events.push_back(ev);
+    }
+    e0 = c->prof_events[c->prof_used];
+    e1 = c->prof_events[c->prof_used + 1];
+    c->prof_used += 2;
+    cudaEventRecord(e0, s);
+  }
   kern<<<(unsigned)grid, p.B * p.nt, smem, s>>>(p);
+  count_launch();
+  if (prof) {
+    cudaEventRecord(e1, s);
+    double fl, by;
+    pass_work<R, TIN, TOUT, FLAGS>(p, fl, by);
+    c->prof_flops += fl;
+    c->prof_bytes += by;
+  }
   return cudaGetLastError();
 }
 

@@ -46,11 +46,13 @@ __global__ void k_axis_tables(const double* __restrict__ c, int n, int L, double
 }
 
 void launch_setup_coefficients(double* c, int nmax, double alpha, cudaStream_t s) {
+  count_launch();
   k_coefficients<<<1, 1, 0, s>>>(c, nmax, alpha);
 }
 
 void launch_setup_axis(const double* c, int n, int L, double* lam, double* circ, double2* tw64, float2* tw32,
                        cudaStream_t s) {
+  count_launch();
   k_axis_tables<<<(L + 127) / 128, 128, 0, s>>>(c, n, L, lam, circ, tw64, tw32);
 }
 

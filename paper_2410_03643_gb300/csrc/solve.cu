@@ -1,5 +1,6 @@
 // Solver drivers: the preconditioner and matrix sequences of line passes, right-preconditioned
 // GMRES (FP64), the mixed-precision FGMRES with FP64 iterative refinement, and the time steps.
+#include <algorithm>
 #include <cmath>
 #include "internal.cuh"
 #include "passes.cuh"
@@ -56,45 +57,45 @@ cudaError_t run_precon(rfnse_ctx* c, const TIN* v, const double* in_scale, doubl
     PassParams p = base_params(c, 0, half, F32);
     p.in = v; p.in_scale = in_scale; p.copy_out = copy_v; p.out = z; p.z_add = z_add; p.D = D;
     p.acc_in = w_add; p.acc_out = w; p.ca = a; p.cb = b;
-    return launch_pass<R, TIN, TZ, IS | F_DST | F_LAM | F_DSCALE | TX>(p, s);
+    return launch_pass<R, TIN, TZ, IS | F_DST | F_LAM | F_DSCALE | TX>(c, p, s);
   }
   // first axis: forward DST (and the Arnoldi normalisation)
   {
     PassParams p = base_params(c, 0, half, F32);
     p.in = v; p.in_scale = in_scale; p.copy_out = copy_v; p.out = t1;
-    if ((e = launch_pass<R, TIN, TMP, IS | F_DST>(p, s)) != cudaSuccess) return e;
+    if ((e = launch_pass<R, TIN, TMP, IS | F_DST>(c, p, s)) != cudaSuccess) return e;
   }
   TMP* cur = t1;
   TMP* nxt = t2;
   for (int a2 = 1; a2 < c->d - 1; ++a2) {  // middle axes (d = 3): forward DST
     PassParams p = base_params(c, a2, half, F32);
     p.in = cur; p.out = nxt;
-    if ((e = launch_pass<R, TMP, TMP, F_DST>(p, s)) != cudaSuccess) return e;
+    if ((e = launch_pass<R, TMP, TMP, F_DST>(c, p, s)) != cudaSuccess) return e;
     TMP* t = cur; cur = nxt; nxt = t;
   }
   {  // last axis: DST, divide by (w + i Lambda), DST
     PassParams p = base_params(c, c->d - 1, half, F32);
     p.in = cur; p.out = nxt;
-    if ((e = launch_pass<R, TMP, TMP, F_DST | F_LAM>(p, s)) != cudaSuccess) return e;
+    if ((e = launch_pass<R, TMP, TMP, F_DST | F_LAM>(c, p, s)) != cudaSuccess) return e;
     TMP* t = cur; cur = nxt; nxt = t;
   }
   for (int a2 = c->d - 2; a2 >= 1; --a2) {  // middle axes: inverse DST (S is involutory)
     PassParams p = base_params(c, a2, half, F32);
     p.in = cur; p.out = nxt;
-    if ((e = launch_pass<R, TMP, TMP, F_DST>(p, s)) != cudaSuccess) return e;
+    if ((e = launch_pass<R, TMP, TMP, F_DST>(c, p, s)) != cudaSuccess) return e;
     TMP* t = cur; cur = nxt; nxt = t;
   }
   {  // first axis: inverse DST, (wI + D)^{-1} sub-solve, optional Toeplitz along x
     PassParams p = base_params(c, 0, half, F32);
     p.in = cur; p.out = z; p.z_add = z_add; p.D = D;
     p.acc_in = w_add; p.acc_out = w; p.ca = a; p.cb = b;
-    if ((e = launch_pass<R, TMP, TZ, F_DST | F_DSCALE | TX>(p, s)) != cudaSuccess) return e;
+    if ((e = launch_pass<R, TMP, TZ, F_DST | F_DSCALE | TX>(c, p, s)) != cudaSuccess) return e;
   }
   if (MATVEC) {
     for (int a2 = 1; a2 < c->d; ++a2) {
       PassParams p = base_params(c, a2, half, F32);
       p.in = z; p.acc_in = w; p.acc_out = w; p.cb = b;
-      if ((e = launch_pass<R, TZ, TZ, F_TOEP_ACC>(p, s)) != cudaSuccess) return e;
+      if ((e = launch_pass<R, TZ, TZ, F_TOEP_ACC>(c, p, s)) != cudaSuccess) return e;
     }
   }
   return cudaSuccess;
@@ -108,12 +109,12 @@ cudaError_t run_matvec_fp64(rfnse_ctx* c, const double2* z, const double* D, dou
   {
     PassParams p = base_params(c, 0, half, false);
     p.in = z; p.D = D; p.acc_in = add; p.acc_out = w; p.ca = a; p.cb = b;
-    if ((e = launch_pass<double, double2, double2, F_TOEP_X>(p, s)) != cudaSuccess) return e;
+    if ((e = launch_pass<double, double2, double2, F_TOEP_X>(c, p, s)) != cudaSuccess) return e;
   }
   for (int a2 = 1; a2 < c->d; ++a2) {
     PassParams p = base_params(c, a2, half, false);
     p.in = z; p.acc_in = w; p.acc_out = w; p.cb = b;
-    if ((e = launch_pass<double, double2, double2, F_TOEP_ACC>(p, s)) != cudaSuccess) return e;
+    if ((e = launch_pass<double, double2, double2, F_TOEP_ACC>(c, p, s)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -122,17 +123,17 @@ cudaError_t run_dst(rfnse_ctx* c, int axis, const double2* in, double2* out, int
   if (precision) {
     PassParams p = base_params(c, axis, 0, true);
     p.in = in; p.out = out;
-    return launch_pass<float, double2, double2, F_DST>(p, c->stream);
+    return launch_pass<float, double2, double2, F_DST>(c, p, c->stream);
   }
   PassParams p = base_params(c, axis, 0, false);
   p.in = in; p.out = out;
-  return launch_pass<double, double2, double2, F_DST>(p, c->stream);
+  return launch_pass<double, double2, double2, F_DST>(c, p, c->stream);
 }
 
 cudaError_t run_toeplitz(rfnse_ctx* c, int axis, const double2* in, double2* out, int half) {
   PassParams p = base_params(c, axis, half, false);
   p.in = in; p.acc_in = nullptr; p.acc_out = out; p.cb = kOne;
-  return launch_pass<double, double2, double2, F_TOEP_ACC>(p, c->stream);
+  return launch_pass<double, double2, double2, F_TOEP_ACC>(c, p, c->stream);
 }
 
 cudaError_t run_apply_prec(rfnse_ctx* c, const double2* v, double2* z, const double* D, int half, int precision) {

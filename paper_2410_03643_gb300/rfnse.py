@@ -51,7 +51,10 @@ class Params(ctypes.Structure):
 
 EXPORTED = ("rfnse_default_params", "rfnse_create", "rfnse_destroy", "rfnse_last_error", "rfnse_size",
             "rfnse_set_state", "rfnse_get_state", "rfnse_run", "rfnse_apply_A", "rfnse_apply_prec",
-            "rfnse_dst", "rfnse_toeplitz", "rfnse_solve", "rfnse_get_coefficients")
+            "rfnse_dst", "rfnse_toeplitz", "rfnse_solve", "rfnse_get_coefficients", "rfnse_launch_count",
+            "rfnse_profile", "rfnse_profile_read")
+
+K_INSCALE, K_DST, K_LAM, K_DSCALE, K_TOEP_X, K_TOEP_ACC, K_FP32 = 1, 2, 4, 8, 16, 32, 256
 
 _lib = None
 
@@ -94,6 +97,12 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.rfnse_solve.restype = ip
     lib.rfnse_get_coefficients.argtypes = [vp, dp, dp]
     lib.rfnse_get_coefficients.restype = ip
+    lib.rfnse_launch_count.argtypes = []
+    lib.rfnse_launch_count.restype = ctypes.c_longlong
+    lib.rfnse_profile.argtypes = [vp, ip]
+    lib.rfnse_profile.restype = ip
+    lib.rfnse_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp, dp, dp]
+    lib.rfnse_profile_read.restype = ip
     if path == _build.library_path():
         _lib = lib
     return lib
@@ -119,6 +128,11 @@ def make_params(problem, precision: int = 0, inner_tol: float = 1e-6, max_outer:
     p.inner_tol = inner_tol
     p.max_outer = max_outer
     return p
+
+
+def launch_count() -> int:
+    """Kernels launched by librfnse.so in this process."""
+    return int(load_library().rfnse_launch_count())
 
 
 def _ptr(t) -> int:
@@ -238,6 +252,18 @@ class Solver:
         self._check(self.lib.rfnse_solve(self.h, _ptr(D), _ptr(b), _ptr(u), int(half), ctypes.byref(it),
                                          ctypes.byref(rr)))
         return u, it.value, rr.value
+
+    def profile(self, kind: int):
+        """Time every launch of kernel class `kind` (K_* flags; 0 = off)."""
+        self._check(self.lib.rfnse_profile(self.h, kind))
+
+    def profile_read(self):
+        """(launches, device ms, algorithmic flops, algorithmic bytes) since profile()."""
+        n = ctypes.c_int()
+        ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.rfnse_profile_read(self.h, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl),
+                                                ctypes.byref(by)))
+        return n.value, ms.value, fl.value, by.value
 
     def coefficients(self):
         nmax = max(self.problem.n[: self.problem.d])
