@@ -140,6 +140,25 @@ int rfnse_solve(rfnse_ctx* ctx, const double* D, const void* b, void* u, int hal
    Either pointer may be NULL. */
 int rfnse_get_coefficients(rfnse_ctx* ctx, double* c, double* lam);
 
+/* z = F~^{-1} v exactly as rfnse_apply_prec with precision 0, but without a context and without
+   allocating any device memory.  (The paper has no counterpart: this is a service for callers that
+   cannot call cudaMalloc -- plug-ins whose host application owns the device-memory budget,
+   real-time loops that must not allocate once running, programs whose memory comes from an
+   allocator other than CUDA's.)  p describes the problem as for rfnse_create (restart, tolerance
+   and precision are ignored); v, z: N complex FP64 device values (may not alias); D: N FP64 device
+   values; stream: cudaStream_t (may be NULL).  Work is issued on stream and the call returns after
+   synchronising it.
+   Scratch: the coefficient, eigenvalue and twiddle tables and the two intermediate grid vectors live
+   in one static device array of about 8.5 MB that every GPU loading this library holds until the
+   process exits.  Limit: N = n[0]*n[1]*n[2] <= 262144 (e.g. 511 x 511), each n[a] + 1 a power of two
+   in [4, 2048]; larger grids return RFNSE_EINVAL (use rfnse_create).  The first call on a device
+   looks up the array's device address (cudaGetSymbolAddress) for that device; make that first call
+   before any stream capture.  All calls on a device share the array and each overwrites what it
+   reads, so nothing needs clearing between calls, but calls whose work overlaps on the GPU race on
+   it: serialise them.  Errors: EINVAL, ECUDA. */
+int rfnse_apply_prec_static(const rfnse_params* p, const void* v, void* z, const double* D, int half,
+                            void* stream);
+
 /* ---- instrumentation -------------------------------------------------------------------------- */
 
 /* Number of CUDA kernels this library has launched in the calling process (all contexts). */

@@ -1,0 +1,122 @@
+// rfnse_apply_prec_static: the preconditioner apply of rfnse_apply_prec (FP64) without any device
+// allocation.  Some callers cannot call cudaMalloc: plug-ins whose host application owns the whole
+// device-memory budget, real-time loops that must not allocate once they are running, and programs
+// whose memory comes from an allocator other than CUDA's.  They still pass their own inputs and
+// outputs; everything else this call needs (the coefficient, eigenvalue and twiddle tables and the
+// two intermediate grid vectors between the line passes) lives in one file-scope device array.
+//
+// The array is a static __device__ object: every GPU that loads this library holds it (about 8.5 MB)
+// until the process exits.  All calls on a device share it, and it keeps whatever the last call
+// wrote; this entry point overwrites every part it reads, so nothing has to start at zero.  Two
+// calls whose work overlaps on the GPU (different streams, or different host threads) race on the
+// array and give wrong results: serialise them.
+#include <cmath>
+#include <mutex>
+#include "internal.cuh"
+#include "solve.cuh"
+
+namespace {
+
+constexpr long long kStaticMaxN = 1LL << 18;   // largest grid: N = n0*n1*n2 <= 262144 complex values
+constexpr int kStaticMaxL = 4096;              // FFT length 2(n+1) for n + 1 <= 2048
+constexpr int kStaticMaxNAxis = 2047;
+
+// Layout of the array, in double2 units:
+//   [t1: kStaticMaxN][t2: kStaticMaxN]
+//   [c: 1024 (2048 doubles)]
+//   per axis a < 3: [lam: 1024 (2048 doubles)][circ: 2048 (4096 doubles)][tw64: 4096][tw32: 2048 (4096 float2)]
+constexpr long long kTableElems = 1024 + 3LL * (1024 + 2048 + 4096 + 2048);
+constexpr long long kStaticElems = 2 * kStaticMaxN + kTableElems;
+
+static __device__ __align__(256) double2 g_prec_scratch[kStaticElems];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_addr_mutex;
+void* g_addr[kMaxDevices] = {};
+
+bool pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Device address of g_prec_scratch on the current device.  Host code may not use the symbol itself
+// (it is a host-side stand-in); cudaGetSymbolAddress gives the real address, once per device.
+cudaError_t scratch_address(double2** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_addr_mutex);
+  if (!g_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_prec_scratch);
+    if (e != cudaSuccess) return e;
+    g_addr[dev] = p;
+  }
+  *out = static_cast<double2*>(g_addr[dev]);
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" int rfnse_apply_prec_static(const rfnse_params* p, const void* v, void* z, const double* D, int half,
+                                       void* stream) {
+  using namespace rfnse;
+  if (!p || !v || !z || !D || v == z) return RFNSE_EINVAL;
+  if (p->d < 1 || p->d > 3) return RFNSE_EINVAL;
+  long long N = 1;
+  for (int a = 0; a < p->d; ++a) {
+    if (p->n[a] < 3 || p->n[a] > kStaticMaxNAxis || !pow2((long long)p->n[a] + 1)) return RFNSE_EINVAL;
+    if (!(p->hi[a] > p->lo[a])) return RFNSE_EINVAL;
+    N *= p->n[a];
+  }
+  if (N > kStaticMaxN) return RFNSE_EINVAL;  // larger grids need rfnse_create / rfnse_apply_prec
+  if (!(p->alpha > 1.0 && p->alpha <= 2.0) || !(p->dt > 0.0) || !(p->omega > 0.0)) return RFNSE_EINVAL;
+
+  double2* base = nullptr;
+  if (scratch_address(&base) != cudaSuccess) return RFNSE_ECUDA;
+
+  // A context on the stack whose arrays all point into the static scratch: no allocation.
+  rfnse_ctx c;
+  c.p = *p;
+  c.p.precision = 0;
+  c.stream = (cudaStream_t)stream;
+  c.d = p->d;
+  c.N = 1;
+  int nmax = 0;
+  for (int a = 0; a < 3; ++a) {
+    c.n[a] = (a < c.d) ? p->n[a] : 1;
+    c.stride[a] = c.N;
+    c.N *= c.n[a];
+    c.L[a] = (a < c.d) ? 2 * (c.n[a] + 1) : 0;
+    c.log2L[a] = 0;
+    while (a < c.d && (1 << c.log2L[a]) < c.L[a]) ++c.log2L[a];
+    c.h[a] = (a < c.d) ? (p->hi[a] - p->lo[a]) / (c.n[a] + 1) : 0.0;
+    c.mu[a] = (a < c.d) ? p->dt / std::pow(c.h[a], p->alpha) : 0.0;
+    if (a < c.d && c.n[a] > nmax) nmax = c.n[a];
+  }
+  c.t1 = base;
+  c.t2 = base + kStaticMaxN;
+  double2* tab = base + 2 * kStaticMaxN;
+  c.c = reinterpret_cast<double*>(tab);
+  tab += 1024;
+  for (int a = 0; a < 3; ++a) {
+    double* lam = reinterpret_cast<double*>(tab);
+    double* circ = reinterpret_cast<double*>(tab + 1024);
+    double2* tw64 = tab + 1024 + 2048;
+    float2* tw32 = reinterpret_cast<float2*>(tab + 1024 + 2048 + kStaticMaxL);
+    tab += 1024 + 2048 + kStaticMaxL + 2048;
+    if (a < c.d) {
+      c.lam[a] = lam;
+      c.circ[a] = circ;
+      c.tw64[a] = tw64;
+      c.tw32[a] = tw32;
+    }
+  }
+
+  // Tables first (they are rewritten on every call), then the same passes as rfnse_apply_prec.
+  launch_setup_coefficients(c.c, nmax, p->alpha, c.stream);
+  for (int a = 0; a < c.d; ++a)
+    launch_setup_axis(c.c, c.n[a], c.L[a], c.lam[a], c.circ[a], c.tw64[a], c.tw32[a], c.stream);
+  if (cudaGetLastError() != cudaSuccess) return RFNSE_ECUDA;
+  if (run_apply_prec(&c, (const double2*)v, (double2*)z, D, half ? 1 : 0, 0) != cudaSuccess) return RFNSE_ECUDA;
+  if (cudaStreamSynchronize(c.stream) != cudaSuccess) return RFNSE_ECUDA;
+  return RFNSE_OK;
+}
