@@ -22,6 +22,7 @@ import statistics
 import subprocess
 import sys
 import threading
+from concurrent.futures import ThreadPoolExecutor
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -47,6 +48,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--serial", action="store_true", help="advance the instances one after another on one stream")
     return ap.parse_args()
 
 
@@ -235,23 +237,40 @@ def run_ours(args):
     from paper_2410_03643_gb300 import build, rfnse
     build.build_library()
     inst, desc = workload(args.workload)
-    stream = torch.cuda.current_stream()
+    main = torch.cuda.current_stream()
+    concurrent = not args.serial and len(inst) > 1
+    pool = ThreadPoolExecutor(max_workers=len(inst)) if concurrent else None
 
     def make(precision):
         solvers = []
         for p, u0 in inst:
-            s = rfnse.Solver(p, precision=precision, stream=stream)
+            st = torch.cuda.Stream(device=dev) if concurrent else main
+            s = rfnse.Solver(p, precision=precision, stream=st)
             s.set_state(torch.from_numpy(u0.ravel().copy()).to(dev))
             solvers.append(s)
+        torch.cuda.synchronize()
         return solvers
+
+    def advance(solvers, start_ev=None):
+        """One bench step: every instance advances one time step (instances in parallel streams)."""
+        if not concurrent:
+            return [int(s.run(1)[0][0]) for s in solvers]
+        if start_ev is not None:
+            for s in solvers:
+                s.stream.wait_event(start_ev)
+        its = [int(f.result()[0][0]) for f in [pool.submit(s.run, 1) for s in solvers]]
+        for s in solvers:
+            ev = torch.cuda.Event()
+            ev.record(s.stream)
+            main.wait_event(ev)
+        return its
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     dof_per_step = sum(p.size for p, _ in inst)
 
     def timed(solvers, steps, warmup, profile_kind=0, clocks=None):
         for _ in range(warmup):
-            for s in solvers:
-                s.run(1)
+            advance(solvers)
         torch.cuda.synchronize()
         if profile_kind:
             for s in solvers:
@@ -266,11 +285,9 @@ def run_ours(args):
         wall0 = time.perf_counter()
         for k in range(steps):
             flush.fill_(float(k))                       # evict L2 between timed steps
-            evs[k][0].record(stream)
-            for s in solvers:
-                it, _ = s.run(1)
-                iters.append(int(it[0]))
-            evs[k][1].record(stream)
+            evs[k][0].record(main)
+            iters += advance(solvers, evs[k][0])
+            evs[k][1].record(main)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
         if clocks:
@@ -305,7 +322,9 @@ def run_ours(args):
            "data": "synthetic (closed-form initial data of the paper's shape)",
            "config": dict(desc, precision="mixed: FP32 transforms in FGMRES, FP64 Arnoldi/Givens/residual",
                           l2="256 MiB buffer written between timed steps",
-                          parallelism=f"{world} GPU(s), instances replicated per GPU"),
+                          parallelism=(f"{world} GPU(s), instances replicated per GPU; "
+                                       + ("one CUDA stream and host thread per instance" if concurrent
+                                          else "instances in turn on one stream"))),
            "gpu_launches": launches,
            "iters_per_solve_mean": float(np.mean(iters_m)) if iters_m else None}
 
@@ -359,12 +378,19 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()
+        def e2e_one(s, h):
+            s.set_state_host(h[1].numpy(), h[0].numpy(), h[3])     # H2D of u^{n-1}, u^n
+            s.run_host(1, h[2].numpy())                            # step + D2H of u^{n+1}
+            h[0], h[1], h[2] = h[1], h[2], h[0]
+            h[3] += 1
+
         for _ in range(steps_e2e):
-            for s, h in zip(e2e_solvers, hosts):
-                s.set_state_host(h[1].numpy(), h[0].numpy(), h[3])
-                s.run_host(1, h[2].numpy())
-                h[0], h[1], h[2] = h[1], h[2], h[0]
-                h[3] += 1
+            if concurrent:
+                for f in [pool.submit(e2e_one, s, h) for s, h in zip(e2e_solvers, hosts)]:
+                    f.result()
+            else:
+                for s, h in zip(e2e_solvers, hosts):
+                    e2e_one(s, h)
         torch.cuda.synchronize()
         e2e_s = reduce_max(time.perf_counter() - t0, world, dev)
         nb = sum(s.N for s in e2e_solvers) * 16

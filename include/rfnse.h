@@ -148,8 +148,8 @@ int rfnse_get_coefficients(rfnse_ctx* ctx, double* c, double* lam);
    and precision are ignored); v, z: N complex FP64 device values (may not alias); D: N FP64 device
    values; stream: cudaStream_t (may be NULL).  Work is issued on stream and the call returns after
    synchronising it.
-   Scratch: the coefficient, eigenvalue and twiddle tables and the two intermediate grid vectors live
-   in one static device array of about 8.5 MB that every GPU loading this library holds until the
+   Scratch: the coefficient, eigenvalue, twiddle and factor tables and the intermediate grid vectors live
+   in one static device array of about 17 MB that every GPU loading this library holds until the
    process exits.  Limit: N = n[0]*n[1]*n[2] <= 262144 (e.g. 511 x 511), each n[a] + 1 a power of two
    in [4, 2048]; larger grids return RFNSE_EINVAL (use rfnse_create).  The first call on a device
    looks up the array's device address (cudaGetSymbolAddress) for that device; make that first call

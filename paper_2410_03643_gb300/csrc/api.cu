@@ -47,6 +47,19 @@ void free_ctx(rfnse_ctx* c) {
   cudaFree(c->Z32);
   cudaFree(c->t1f);
   cudaFree(c->t2f);
+  cudaFree(c->wp32);
+  for (int i = 0; i < 3; ++i) cudaFree(c->Tu[i]);
+  cudaFree(c->D32);
+  cudaFree(c->dfac64);
+  cudaFree(c->dfac32);
+  for (int h = 0; h < 2; ++h) {
+    cudaFree(c->lamfac64[h]);
+    cudaFree(c->lamfac32[h]);
+    for (int a = 0; a < 3; ++a) {
+      cudaFree(c->circ64s[h][a]);
+      cudaFree(c->circ32s[h][a]);
+    }
+  }
   cudaFree(c->partials);
   cudaFree(c->counter);
   cudaFree(c->gs);
@@ -160,6 +173,20 @@ int rfnse_create(const rfnse_params* p, void* stream, rfnse_ctx** out) {
   chk(dalloc(&c->t1f, N));
   chk(dalloc(&c->t2f, N));
   if (p->precision == 1) chk(dalloc(&c->Z32, (size_t)m * N));
+  chk(dalloc(&c->wp32, N));
+  if (p->precision == 1)
+    for (int i = 0; i < 3; ++i) chk(dalloc(&c->Tu[i], N));
+  chk(dalloc(&c->D32, N));
+  chk(dalloc(&c->dfac64, N));
+  chk(dalloc(&c->dfac32, N));
+  for (int h = 0; h < 2; ++h) {
+    chk(dalloc(&c->lamfac64[h], N));
+    chk(dalloc(&c->lamfac32[h], N));
+    for (int a = 0; a < c->d; ++a) {
+      chk(dalloc(&c->circ64s[h][a], c->L[a]));
+      chk(dalloc(&c->circ32s[h][a], c->L[a]));
+    }
+  }
   c->red_blocks = choose_reduce_blocks(N);
   chk(dalloc(&c->partials, 1024));
   chk(dalloc(&c->counter, 1));
@@ -178,6 +205,15 @@ int rfnse_create(const rfnse_params* p, void* stream, rfnse_ctx** out) {
   launch_setup_coefficients(c->c, nmax, p->alpha, c->stream);
   for (int a = 0; a < c->d; ++a)
     launch_setup_axis(c->c, c->n[a], c->L[a], c->lam[a], c->circ[a], c->tw64[a], c->tw32[a], c->stream);
+  for (int h = 0; h < 2; ++h) {  // h = 1: the first step's mu_a / 2
+    const double hf = h ? 0.5 : 1.0;
+    launch_setup_lamfac(c->lam[0], c->lam[1], c->lam[2], c->n[0], c->n[1], c->n[2], hf * c->mu[0], hf * c->mu[1],
+                        hf * c->mu[2], p->omega, 1.0 / std::sqrt((double)c->L[c->d - 1]), c->lamfac64[h],
+                        c->lamfac32[h], N, c->stream);
+    for (int a = 0; a < c->d; ++a)
+      launch_scale_circ(c->circ[a], c->L[a], hf * c->mu[a] / c->L[a], c->circ64s[h][a], c->circ32s[h][a],
+                        c->stream);
+  }
   chk(cudaGetLastError());
   chk(cudaStreamSynchronize(c->stream));
   if (e != cudaSuccess) {
@@ -212,6 +248,7 @@ int rfnse_set_state(rfnse_ctx* c, const void* u_prev, const void* u_cur, int ste
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   c->iprev = 0;
   c->icur = 1;
+  for (int i = 0; i < 3; ++i) c->tu_valid[i] = false;
   if (step > 0) RFNSE_CUDA_TRY(c, cudaMemcpyAsync(c->u[c->iprev], u_prev, bytes, kind, c->stream));
   RFNSE_CUDA_TRY(c, cudaMemcpyAsync(c->u[c->icur], u_cur, bytes, kind, c->stream));
   RFNSE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));

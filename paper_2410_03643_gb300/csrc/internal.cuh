@@ -40,9 +40,9 @@ struct GmresPeek {
 };
 
 inline int choose_reduce_blocks(long long N) {
-  long long b = (N + 2047) / 2048;
+  long long b = (N + 511) / 512;   // enough blocks to cover all 152 SMs; fixed for a given N
   if (b < 1) b = 1;
-  if (b > 1024) b = 1024;
+  if (b > 4 * 152) b = 4 * 152;
   return (int)b;
 }
 
@@ -64,11 +64,26 @@ void launch_diag(const double2* u, const double2* u2, double* D, double rho_dt, 
 void launch_neg_i(const double2* b, double2* f, long long N, cudaStream_t s);
 void launch_zero(double2* x, long long N, cudaStream_t s);
 void launch_start_cycle(GmresState* gs, double ref, double tol, cudaStream_t s);
+// Tu = scale (D x - i (f - x - r)) from the residual r = f - x - i(T - D)x
+void launch_tu_from_residual(const double* D, const double2* f, const double2* x, const double2* r, double2* Tu,
+                             double scale, long long N, cudaStream_t s);
+// f = u - i (Tu - D u)
+void launch_rhs_from_tu(const double2* u, const double2* Tu, const double* D, double2* f, long long N,
+                        cudaStream_t s);
+// D32 = D, dfac = 2w((w+1) + iD)/((w+1)^2 + D^2) in FP64 and FP32
+void launch_prep_D(const double* D, float* D32, double2* dfac64, float2* dfac32, double omega, long long N,
+                   cudaStream_t s);
 
 // ---- setup kernels (setup.cu) -------------------------------------------------------------------
 void launch_setup_coefficients(double* c, int nmax, double alpha, cudaStream_t s);
 void launch_setup_axis(const double* c, int n, int L, double* lam, double* circ, double2* tw64, float2* tw32,
                        cudaStream_t s);
+// lamfac[g] = i dst_scale / (w + i sum_a mu_a lambda_a(k_a(g))) for every grid index g
+void launch_setup_lamfac(const double* lam0, const double* lam1, const double* lam2, int n0, int n1, int n2,
+                         double mu0, double mu1, double mu2, double omega, double dst_scale, double2* f64,
+                         float2* f32, long long N, cudaStream_t s);
+// scaled circulant spectrum circ * scale in FP64 and FP32
+void launch_scale_circ(const double* circ, int L, double scale, double* c64, float* c32, cudaStream_t s);
 
 }  // namespace rfnse
 
@@ -97,6 +112,20 @@ struct rfnse_ctx {
   double2* V = nullptr;     // (m + 1) Krylov vectors
   float2* Z32 = nullptr;    // m preconditioned vectors of the mixed form
   float2 *t1f = nullptr, *t2f = nullptr;
+  float2* wp32 = nullptr;   // FP32 partial matrix product between the Toeplitz passes (mixed form)
+  // per-point factor tables in both precisions
+  float* D32 = nullptr;                     // D of the current solve
+  double2* dfac64 = nullptr;                // 2w((w+1) + iD)/((w+1)^2 + D^2) of the current solve
+  float2* dfac32 = nullptr;
+  double2* lamfac64[2] = {nullptr, nullptr};  // i dst_scale/(w + i Lambda(k)) per mode; [half]
+  float2* lamfac32[2] = {nullptr, nullptr};
+  double* circ64s[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};  // circ * mu_a hf / L
+  float* circ32s[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  // mixed form: T u of each history vector, recovered from the final FP64 residual of the solve
+  // that produced it (so the right-hand side two steps later needs no Toeplitz product)
+  double2* Tu[3] = {nullptr, nullptr, nullptr};
+  bool tu_valid[3] = {false, false, false};
+  bool resid_current = false;               // c->r holds f - R x for the last solve's x
   double* partials = nullptr;
   unsigned* counter = nullptr;
   int red_blocks = 1;

@@ -215,6 +215,45 @@ __global__ void k_neg_i(const double2* __restrict__ b, double2* __restrict__ f, 
   }
 }
 
+// D in FP32 and the per-point factor of the (omega I + D_d) sub-solve with the 2 omega of F~^{-1}
+// (eq. 'taupre'): 2w/((w+1) - iD) = 2w((w+1) + iD)/((w+1)^2 + D^2), in FP64 and FP32.
+__global__ void k_prep_D(const double* __restrict__ D, float* __restrict__ D32, double2* __restrict__ dfac64,
+                         float2* __restrict__ dfac32, double omega, long long N) {
+  const double w1 = omega + 1.0, two_w = 2.0 * omega;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double d = D[i];
+    const double s = two_w / (w1 * w1 + d * d);
+    const double2 f = make_double2(s * w1, s * d);
+    D32[i] = (float)d;
+    dfac64[i] = f;
+    dfac32[i] = make_float2((float)f.x, (float)f.y);
+  }
+}
+
+// From the final FP64 residual r = f - x - i(T - D)x of a solve: Tx = s (D x - i (f - x - r)).
+// (s = 2 turns the first step's (T/2) x into T x.)
+__global__ void k_tu_from_residual(const double* __restrict__ D, const double2* __restrict__ f,
+                                   const double2* __restrict__ x, const double2* __restrict__ r,
+                                   double2* __restrict__ Tu, double s, long long N) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double2 fv = f[i], xv = x[i], rv = r[i];
+    const double d = D[i];
+    const double qx = fv.x - xv.x - rv.x, qy = fv.y - xv.y - rv.y;
+    Tu[i] = make_double2(s * (d * xv.x + qy), s * (d * xv.y - qx));
+  }
+}
+
+// Right-hand side f = u - i (T u - D u) from a cached T u.
+__global__ void k_rhs_from_tu(const double2* __restrict__ u, const double2* __restrict__ Tu,
+                              const double* __restrict__ D, double2* __restrict__ f, long long N) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double2 uv = u[i], tv = Tu[i];
+    const double d = D[i];
+    const double px = tv.x - d * uv.x, py = tv.y - d * uv.y;
+    f[i] = make_double2(uv.x + py, uv.y - px);
+  }
+}
+
 __global__ void k_zero(double2* __restrict__ x, long long N) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
     x[i] = make_double2(0.0, 0.0);
@@ -264,6 +303,21 @@ void launch_diag(const double2* u, const double2* u2, double* D, double rho_dt, 
 void launch_neg_i(const double2* b, double2* f, long long N, cudaStream_t s) {
   count_launch();
   k_neg_i<<<ew_blocks(N), 256, 0, s>>>(b, f, N);
+}
+void launch_prep_D(const double* D, float* D32, double2* dfac64, float2* dfac32, double omega, long long N,
+                   cudaStream_t s) {
+  count_launch();
+  k_prep_D<<<ew_blocks(N), 256, 0, s>>>(D, D32, dfac64, dfac32, omega, N);
+}
+void launch_tu_from_residual(const double* D, const double2* f, const double2* x, const double2* r, double2* Tu,
+                             double scale, long long N, cudaStream_t s) {
+  count_launch();
+  k_tu_from_residual<<<ew_blocks(N), 256, 0, s>>>(D, f, x, r, Tu, scale, N);
+}
+void launch_rhs_from_tu(const double2* u, const double2* Tu, const double* D, double2* f, long long N,
+                        cudaStream_t s) {
+  count_launch();
+  k_rhs_from_tu<<<ew_blocks(N), 256, 0, s>>>(u, Tu, D, f, N);
 }
 void launch_zero(double2* x, long long N, cudaStream_t s) { k_zero<<<ew_blocks(N), 256, 0, s>>>(x, N); }
 

@@ -2,10 +2,10 @@
 // allocation.  Some callers cannot call cudaMalloc: plug-ins whose host application owns the whole
 // device-memory budget, real-time loops that must not allocate once they are running, and programs
 // whose memory comes from an allocator other than CUDA's.  They still pass their own inputs and
-// outputs; everything else this call needs (the coefficient, eigenvalue and twiddle tables and the
-// two intermediate grid vectors between the line passes) lives in one file-scope device array.
+// outputs; everything else this call needs (the coefficient, eigenvalue, twiddle and factor tables
+// and the intermediate grid vectors between the line passes) lives in one file-scope device array.
 //
-// The array is a static __device__ object: every GPU that loads this library holds it (about 8.5 MB)
+// The array is a static __device__ object: every GPU that loads this library holds it (about 17 MB)
 // until the process exits.  All calls on a device share it, and it keeps whatever the last call
 // wrote; this entry point overwrites every part it reads, so nothing has to start at zero.  Two
 // calls whose work overlaps on the GPU (different streams, or different host threads) race on the
@@ -22,11 +22,13 @@ constexpr int kStaticMaxL = 4096;              // FFT length 2(n+1) for n + 1 <=
 constexpr int kStaticMaxNAxis = 2047;
 
 // Layout of the array, in double2 units:
-//   [t1: kStaticMaxN][t2: kStaticMaxN]
+//   [t1: kStaticMaxN][t2: kStaticMaxN][dfac64: kStaticMaxN][lamfac64: kStaticMaxN]
 //   [c: 1024 (2048 doubles)]
 //   per axis a < 3: [lam: 1024 (2048 doubles)][circ: 2048 (4096 doubles)][tw64: 4096][tw32: 2048 (4096 float2)]
+// The FP32 companions the set-up kernels also write (lamfac32, D32, dfac32) are not read by this FP64
+// path; they are pointed at t1 and t2, which the first passes overwrite.
 constexpr long long kTableElems = 1024 + 3LL * (1024 + 2048 + 4096 + 2048);
-constexpr long long kStaticElems = 2 * kStaticMaxN + kTableElems;
+constexpr long long kStaticElems = 4 * kStaticMaxN + kTableElems;
 
 static __device__ __align__(256) double2 g_prec_scratch[kStaticElems];
 
@@ -94,7 +96,13 @@ extern "C" int rfnse_apply_prec_static(const rfnse_params* p, const void* v, voi
   }
   c.t1 = base;
   c.t2 = base + kStaticMaxN;
-  double2* tab = base + 2 * kStaticMaxN;
+  c.dfac64 = base + 2 * kStaticMaxN;
+  const int hidx = half ? 1 : 0;
+  c.lamfac64[hidx] = base + 3 * kStaticMaxN;
+  c.lamfac32[hidx] = reinterpret_cast<float2*>(c.t1);
+  c.dfac32 = reinterpret_cast<float2*>(c.t2);                       // 8 N bytes
+  c.D32 = reinterpret_cast<float*>(c.t2) + 2 * kStaticMaxN;          // 4 N bytes after dfac32
+  double2* tab = base + 4 * kStaticMaxN;
   c.c = reinterpret_cast<double*>(tab);
   tab += 1024;
   for (int a = 0; a < 3; ++a) {
@@ -115,6 +123,10 @@ extern "C" int rfnse_apply_prec_static(const rfnse_params* p, const void* v, voi
   launch_setup_coefficients(c.c, nmax, p->alpha, c.stream);
   for (int a = 0; a < c.d; ++a)
     launch_setup_axis(c.c, c.n[a], c.L[a], c.lam[a], c.circ[a], c.tw64[a], c.tw32[a], c.stream);
+  const double hf = half ? 0.5 : 1.0;
+  launch_setup_lamfac(c.lam[0], c.lam[1], c.lam[2], c.n[0], c.n[1], c.n[2], hf * c.mu[0], hf * c.mu[1],
+                      hf * c.mu[2], p->omega, 1.0 / std::sqrt((double)c.L[c.d - 1]), c.lamfac64[hidx],
+                      c.lamfac32[hidx], c.N, c.stream);
   if (cudaGetLastError() != cudaSuccess) return RFNSE_ECUDA;
   if (run_apply_prec(&c, (const double2*)v, (double2*)z, D, half ? 1 : 0, 0) != cudaSuccess) return RFNSE_ECUDA;
   if (cudaStreamSynchronize(c.stream) != cudaSuccess) return RFNSE_ECUDA;

@@ -45,6 +45,56 @@ __global__ void k_axis_tables(const double* __restrict__ c, int n, int L, double
   tw32[k] = make_float2((float)cs, (float)-sn);
 }
 
+// Per-mode factor of the (omega I + tau(T_d)) sub-solve in the DST basis (eq. 'taupre', '2Dtau'):
+//   lamfac[g] = i dst_scale / (omega + i Lambda),  Lambda = sum_a mu_a lambda_a(k_a),
+// where (k_0, k_1, k_2) are the (0-based) mode indices of grid index g, x fastest.  i dst_scale is
+// the output scale of the DST-I computed from an FFT (folded in so the pass multiplies once).
+__global__ void k_lamfac(const double* __restrict__ lam0, const double* __restrict__ lam1,
+                         const double* __restrict__ lam2, int n0, int n1, int n2, double mu0, double mu1,
+                         double mu2, double omega, double dst_scale, double2* __restrict__ f64,
+                         float2* __restrict__ f32, long long N) {
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
+    long long r = g;
+    const int k0 = (int)(r % n0);
+    r /= n0;
+    const int k1 = (int)(r % n1);
+    r /= n1;
+    const int k2 = (int)r;
+    double lam = mu0 * lam0[k0];
+    if (lam1) lam += mu1 * lam1[k1];
+    if (lam2) lam += mu2 * lam2[k2];
+    // i s/(w + i lam) = s (lam + i w)/(w^2 + lam^2)
+    const double den = omega * omega + lam * lam;
+    const double2 f = make_double2(dst_scale * lam / den, dst_scale * omega / den);
+    f64[g] = f;
+    f32[g] = make_float2((float)f.x, (float)f.y);
+  }
+}
+
+__global__ void k_scale_circ(const double* __restrict__ circ, int L, double scale, double* __restrict__ c64,
+                             float* __restrict__ c32) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= L) return;
+  const double v = circ[k] * scale;
+  c64[k] = v;
+  c32[k] = (float)v;
+}
+
+void launch_setup_lamfac(const double* lam0, const double* lam1, const double* lam2, int n0, int n1, int n2,
+                         double mu0, double mu1, double mu2, double omega, double dst_scale, double2* f64,
+                         float2* f32, long long N, cudaStream_t s) {
+  long long blocks = (N + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  count_launch();
+  k_lamfac<<<(unsigned)blocks, 256, 0, s>>>(lam0, lam1, lam2, n0, n1, n2, mu0, mu1, mu2, omega, dst_scale, f64,
+                                           f32, N);
+}
+
+void launch_scale_circ(const double* circ, int L, double scale, double* c64, float* c32, cudaStream_t s) {
+  count_launch();
+  k_scale_circ<<<(L + 127) / 128, 128, 0, s>>>(circ, L, scale, c64, c32);
+}
+
 void launch_setup_coefficients(double* c, int nmax, double alpha, cudaStream_t s) {
   count_launch();
   k_coefficients<<<1, 1, 0, s>>>(c, nmax, alpha);

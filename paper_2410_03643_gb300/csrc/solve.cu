@@ -13,89 +13,112 @@ static const double2 kI = {0.0, 1.0};
 static const double2 kMinusOne = {-1.0, 0.0};
 static const double2 kMinusI = {0.0, -1.0};
 
-PassParams base_params(const rfnse_ctx* c, int axis, int half, bool fp32) {
+template <typename R> struct Tables;
+template <> struct Tables<double> {
+  static const void* tw(const rfnse_ctx* c, int a) { return c->tw64[a]; }
+  static const void* circ(const rfnse_ctx* c, int h, int a) { return c->circ64s[h][a]; }
+  static const void* lamfac(const rfnse_ctx* c, int h) { return c->lamfac64[h]; }
+  static const void* dfac(const rfnse_ctx* c) { return c->dfac64; }
+  static const void* Dr(const rfnse_ctx* c, const double* D) { return D; }
+};
+template <> struct Tables<float> {
+  static const void* tw(const rfnse_ctx* c, int a) { return c->tw32[a]; }
+  static const void* circ(const rfnse_ctx* c, int h, int a) { return c->circ32s[h][a]; }
+  static const void* lamfac(const rfnse_ctx* c, int h) { return c->lamfac32[h]; }
+  static const void* dfac(const rfnse_ctx* c) { return c->dfac32; }
+  static const void* Dr(const rfnse_ctx* c, const double*) { return c->D32; }
+};
+
+template <typename R>
+PassParams base_params(const rfnse_ctx* c, int axis, int half) {
   PassParams p{};
-  const double hf = half ? 0.5 : 1.0;
-  p.d = c->d;
-  p.axis = axis;
-  for (int a = 0; a < 3; ++a) {
-    p.n_ax[a] = (a < c->d) ? c->n[a] : 1;
-    p.lam[a] = (a < c->d) ? c->lam[a] : nullptr;
-    p.mu[a] = (a < c->d) ? c->mu[a] * hf : 0.0;
-  }
   p.n = c->n[axis];
   p.L = c->L[axis];
   p.log2L = c->log2L[axis];
   p.stride = c->stride[axis];
   p.nlines = c->N / c->n[axis];
-  p.tw = fp32 ? (const void*)c->tw32[axis] : (const void*)c->tw64[axis];
-  p.circ = c->circ[axis];
-  p.omega = c->p.omega;
-  p.toep_scale = p.mu[axis] / (double)p.L;
+  p.tw = Tables<R>::tw(c, axis);
+  p.circ = Tables<R>::circ(c, half ? 1 : 0, axis);
   p.dst_scale = 1.0 / std::sqrt((double)p.L);
   p.ca = kOne;
   p.cb = kI;
   return p;
 }
 
+// The per-point factors of the (omega I + D) sub-solve for diagonal D (recomputed when D changes).
+cudaError_t prepare_D(rfnse_ctx* c, const double* D) {
+  launch_prep_D(D, c->D32, c->dfac64, c->dfac32, c->p.omega, c->N, c->stream);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------------------------
 // z = F~^{-1} v (eq. 'taupre'), optionally followed by w = add + a z + b (T - D) z.
-//   R    compute precision of the transforms
-//   TIN  storage of v (double2 when INSC: v is scaled by *in_scale and copied to copy_v)
-//   TMP  storage of the intermediate vectors t1, t2
-//   TZ   storage of z
-template <typename R, typename TIN, typename TMP, typename TZ, bool INSC, bool MATVEC>
+//   R     compute precision of the transforms
+//   TIN   storage of v (double2 when INSC: v is scaled by *in_scale and copied to copy_v)
+//   TMP   storage of the intermediate vectors t1, t2
+//   TZ    storage of z
+//   TW    storage of the partial products between Toeplitz passes (w itself when TW = double2)
+// The caller has run prepare_D for D.
+template <typename R, typename TIN, typename TMP, typename TZ, typename TW, bool INSC, bool MATVEC>
 cudaError_t run_precon(rfnse_ctx* c, const TIN* v, const double* in_scale, double2* copy_v, TZ* z, int z_add,
-                       const double* D, double2* w, const double2* w_add, double2 a, double2 b, int half, TMP* t1,
-                       TMP* t2) {
-  constexpr bool F32 = sizeof(R) == 4;
+                       const double* D, double2* w, TW* wtmp, const double2* w_add, double2 a, double2 b, int half,
+                       TMP* t1, TMP* t2) {
   cudaStream_t s = c->stream;
   cudaError_t e;
   constexpr int IS = INSC ? F_INSCALE : 0;
   constexpr int TX = MATVEC ? F_TOEP_X : 0;
+  const int h = half ? 1 : 0;
   if (c->d == 1) {
-    PassParams p = base_params(c, 0, half, F32);
-    p.in = v; p.in_scale = in_scale; p.copy_out = copy_v; p.out = z; p.z_add = z_add; p.D = D;
+    PassParams p = base_params<R>(c, 0, h);
+    p.in = v; p.in_scale = in_scale; p.copy_out = copy_v; p.out = z; p.z_add = z_add;
+    p.Dr = Tables<R>::Dr(c, D); p.dfac = Tables<R>::dfac(c); p.lamfac = Tables<R>::lamfac(c, h);
     p.acc_in = w_add; p.acc_out = w; p.ca = a; p.cb = b;
-    return launch_pass<R, TIN, TZ, IS | F_DST | F_LAM | F_DSCALE | TX>(c, p, s);
+    return launch_pass<R, TIN, TZ, double2, double2, IS | F_DST | F_LAM | F_DSCALE | TX>(c, p, s);
   }
-  // first axis: forward DST (and the Arnoldi normalisation)
-  {
-    PassParams p = base_params(c, 0, half, F32);
+  {  // first axis: forward DST (and the Arnoldi normalisation)
+    PassParams p = base_params<R>(c, 0, h);
     p.in = v; p.in_scale = in_scale; p.copy_out = copy_v; p.out = t1;
-    if ((e = launch_pass<R, TIN, TMP, IS | F_DST>(c, p, s)) != cudaSuccess) return e;
+    if ((e = launch_pass<R, TIN, TMP, double2, double2, IS | F_DST>(c, p, s)) != cudaSuccess) return e;
   }
   TMP* cur = t1;
   TMP* nxt = t2;
   for (int a2 = 1; a2 < c->d - 1; ++a2) {  // middle axes (d = 3): forward DST
-    PassParams p = base_params(c, a2, half, F32);
+    PassParams p = base_params<R>(c, a2, h);
     p.in = cur; p.out = nxt;
-    if ((e = launch_pass<R, TMP, TMP, F_DST>(c, p, s)) != cudaSuccess) return e;
-    TMP* t = cur; cur = nxt; nxt = t;
+    if ((e = launch_pass<R, TMP, TMP, double2, double2, F_DST>(c, p, s)) != cudaSuccess) return e;
+    std::swap(cur, nxt);
   }
-  {  // last axis: DST, divide by (w + i Lambda), DST
-    PassParams p = base_params(c, c->d - 1, half, F32);
-    p.in = cur; p.out = nxt;
-    if ((e = launch_pass<R, TMP, TMP, F_DST | F_LAM>(c, p, s)) != cudaSuccess) return e;
-    TMP* t = cur; cur = nxt; nxt = t;
+  {  // last axis: DST, multiply by i s/(w + i Lambda), DST
+    PassParams p = base_params<R>(c, c->d - 1, h);
+    p.in = cur; p.out = nxt; p.lamfac = Tables<R>::lamfac(c, h);
+    if ((e = launch_pass<R, TMP, TMP, double2, double2, F_DST | F_LAM>(c, p, s)) != cudaSuccess) return e;
+    std::swap(cur, nxt);
   }
   for (int a2 = c->d - 2; a2 >= 1; --a2) {  // middle axes: inverse DST (S is involutory)
-    PassParams p = base_params(c, a2, half, F32);
+    PassParams p = base_params<R>(c, a2, h);
     p.in = cur; p.out = nxt;
-    if ((e = launch_pass<R, TMP, TMP, F_DST>(c, p, s)) != cudaSuccess) return e;
-    TMP* t = cur; cur = nxt; nxt = t;
+    if ((e = launch_pass<R, TMP, TMP, double2, double2, F_DST>(c, p, s)) != cudaSuccess) return e;
+    std::swap(cur, nxt);
   }
   {  // first axis: inverse DST, (wI + D)^{-1} sub-solve, optional Toeplitz along x
-    PassParams p = base_params(c, 0, half, F32);
-    p.in = cur; p.out = z; p.z_add = z_add; p.D = D;
-    p.acc_in = w_add; p.acc_out = w; p.ca = a; p.cb = b;
-    if ((e = launch_pass<R, TMP, TZ, F_DST | F_DSCALE | TX>(c, p, s)) != cudaSuccess) return e;
+    PassParams p = base_params<R>(c, 0, h);
+    p.in = cur; p.out = z; p.z_add = z_add;
+    p.Dr = Tables<R>::Dr(c, D); p.dfac = Tables<R>::dfac(c);
+    p.acc_in = w_add; p.acc_out = wtmp; p.ca = a; p.cb = b;
+    if ((e = launch_pass<R, TMP, TZ, double2, TW, F_DST | F_DSCALE | TX>(c, p, s)) != cudaSuccess) return e;
   }
   if (MATVEC) {
     for (int a2 = 1; a2 < c->d; ++a2) {
-      PassParams p = base_params(c, a2, half, F32);
-      p.in = z; p.acc_in = w; p.acc_out = w; p.cb = b;
-      if ((e = launch_pass<R, TZ, TZ, F_TOEP_ACC>(c, p, s)) != cudaSuccess) return e;
+      PassParams p = base_params<R>(c, a2, h);
+      p.in = z; p.acc_in = wtmp; p.cb = b;
+      if (a2 == c->d - 1) {
+        p.acc_out = w;
+        e = launch_pass<R, TZ, TZ, TW, double2, F_TOEP_ACC>(c, p, s);
+      } else {
+        p.acc_out = wtmp;
+        e = launch_pass<R, TZ, TZ, TW, TW, F_TOEP_ACC>(c, p, s);
+      }
+      if (e != cudaSuccess) return e;
     }
   }
   return cudaSuccess;
@@ -106,44 +129,47 @@ cudaError_t run_matvec_fp64(rfnse_ctx* c, const double2* z, const double* D, dou
                             double2 a, double2 b, int half) {
   cudaStream_t s = c->stream;
   cudaError_t e;
+  const int h = half ? 1 : 0;
   {
-    PassParams p = base_params(c, 0, half, false);
-    p.in = z; p.D = D; p.acc_in = add; p.acc_out = w; p.ca = a; p.cb = b;
-    if ((e = launch_pass<double, double2, double2, F_TOEP_X>(c, p, s)) != cudaSuccess) return e;
+    PassParams p = base_params<double>(c, 0, h);
+    p.in = z; p.Dr = D; p.acc_in = add; p.acc_out = w; p.ca = a; p.cb = b;
+    if ((e = launch_pass<double, double2, double2, double2, double2, F_TOEP_X>(c, p, s)) != cudaSuccess) return e;
   }
   for (int a2 = 1; a2 < c->d; ++a2) {
-    PassParams p = base_params(c, a2, half, false);
+    PassParams p = base_params<double>(c, a2, h);
     p.in = z; p.acc_in = w; p.acc_out = w; p.cb = b;
-    if ((e = launch_pass<double, double2, double2, F_TOEP_ACC>(c, p, s)) != cudaSuccess) return e;
+    if ((e = launch_pass<double, double2, double2, double2, double2, F_TOEP_ACC>(c, p, s)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
 cudaError_t run_dst(rfnse_ctx* c, int axis, const double2* in, double2* out, int precision) {
   if (precision) {
-    PassParams p = base_params(c, axis, 0, true);
+    PassParams p = base_params<float>(c, axis, 0);
     p.in = in; p.out = out;
-    return launch_pass<float, double2, double2, F_DST>(c, p, c->stream);
+    return launch_pass<float, double2, double2, double2, double2, F_DST>(c, p, c->stream);
   }
-  PassParams p = base_params(c, axis, 0, false);
+  PassParams p = base_params<double>(c, axis, 0);
   p.in = in; p.out = out;
-  return launch_pass<double, double2, double2, F_DST>(c, p, c->stream);
+  return launch_pass<double, double2, double2, double2, double2, F_DST>(c, p, c->stream);
 }
 
 cudaError_t run_toeplitz(rfnse_ctx* c, int axis, const double2* in, double2* out, int half) {
-  PassParams p = base_params(c, axis, half, false);
+  PassParams p = base_params<double>(c, axis, half ? 1 : 0);
   p.in = in; p.acc_in = nullptr; p.acc_out = out; p.cb = kOne;
-  return launch_pass<double, double2, double2, F_TOEP_ACC>(c, p, c->stream);
+  return launch_pass<double, double2, double2, double2, double2, F_TOEP_ACC>(c, p, c->stream);
 }
 
 cudaError_t run_apply_prec(rfnse_ctx* c, const double2* v, double2* z, const double* D, int half, int precision) {
+  cudaError_t e = prepare_D(c, D);
+  if (e != cudaSuccess) return e;
   if (precision) {
     if (!c->t1f) return cudaErrorInvalidValue;
-    return run_precon<float, double2, float2, double2, false, false>(c, v, nullptr, nullptr, z, 0, D, nullptr,
-                                                                     nullptr, kOne, kI, half, c->t1f, c->t2f);
+    return run_precon<float, double2, float2, double2, float2, false, false>(
+        c, v, nullptr, nullptr, z, 0, D, nullptr, nullptr, nullptr, kOne, kI, half, c->t1f, c->t2f);
   }
-  return run_precon<double, double2, double2, double2, false, false>(c, v, nullptr, nullptr, z, 0, D, nullptr,
-                                                                     nullptr, kOne, kI, half, c->t1, c->t2);
+  return run_precon<double, double2, double2, double2, double2, false, false>(
+      c, v, nullptr, nullptr, z, 0, D, nullptr, nullptr, nullptr, kOne, kI, half, c->t1, c->t2);
 }
 
 cudaError_t run_apply_A(rfnse_ctx* c, const double2* u, double2* out, const double* D, int half) {
@@ -201,9 +227,9 @@ static rfnse_status gmres_fp64(rfnse_ctx* c, const double* D, const double2* f, 
     int done = 0;
     double rel = beta / fnorm;
     for (int j = 0; j < m; ++j) {
-      RFNSE_CUDA_TRY(c, (run_precon<double, double2, double2, double2, true, true>(
-                            c, src, scale, c->V + (size_t)j * N, c->zb, 0, D, c->w, nullptr, kOne, kI, half, c->t1,
-                            c->t2)));
+      RFNSE_CUDA_TRY(c, (run_precon<double, double2, double2, double2, double2, true, true>(
+                            c, src, scale, c->V + (size_t)j * N, c->zb, 0, D, c->w, c->w, nullptr, kOne, kI, half,
+                            c->t1, c->t2)));
       arnoldi_orthogonalise(c, j);
       if ((st = peek(c, &pk))) return st;
       ++it;
@@ -217,8 +243,9 @@ static rfnse_status gmres_fp64(rfnse_ctx* c, const double* D, const double2* f, 
     }
     launch_backsolve(c->gs, k, c->stream);
     launch_combine(c->V, N, c->gs, k, c->r, N, c->stream);
-    RFNSE_CUDA_TRY(c, (run_precon<double, double2, double2, double2, false, false>(
-                          c, c->r, nullptr, nullptr, x, 1, D, nullptr, nullptr, kOne, kI, half, c->t1, c->t2)));
+    RFNSE_CUDA_TRY(c, (run_precon<double, double2, double2, double2, double2, false, false>(
+                          c, c->r, nullptr, nullptr, x, 1, D, nullptr, nullptr, nullptr, kOne, kI, half, c->t1,
+                          c->t2)));
     *relres = rel;
     if (done) break;
     if (it >= c->p.max_it) {
@@ -251,6 +278,7 @@ static rfnse_status solve_mixed(rfnse_ctx* c, const double* D, const double2* f,
   const double eta_min = c->p.inner_tol > 0 ? c->p.inner_tol : 1e-6;
   const int max_outer = c->p.max_outer > 0 ? c->p.max_outer : 30;
   GmresPeek pk;
+  c->resid_current = false;
   launch_zero(x, N, c->stream);
   launch_norm(f, c->gs, N, c->red_blocks, c->partials, c->counter, c->stream);
   rfnse_status st = peek(c, &pk);
@@ -279,9 +307,9 @@ static rfnse_status solve_mixed(rfnse_ctx* c, const double* D, const double2* f,
     const double* scale = &c->gs->inv_beta;
     int k = 0;
     for (int j = 0; j < m && it < c->p.max_it; ++j) {
-      RFNSE_CUDA_TRY(c, (run_precon<float, double2, float2, float2, true, true>(
-                            c, src, scale, c->V + (size_t)j * N, c->Z32 + (size_t)j * N, 0, D, c->w, nullptr, kOne,
-                            kI, half, c->t1f, c->t2f)));
+      RFNSE_CUDA_TRY(c, (run_precon<float, double2, float2, float2, float2, true, true>(
+                            c, src, scale, c->V + (size_t)j * N, c->Z32 + (size_t)j * N, 0, D, c->w, c->wp32,
+                            nullptr, kOne, kI, half, c->t1f, c->t2f)));
       arnoldi_orthogonalise(c, j);
       if ((st = peek(c, &pk))) return st;
       ++it;
@@ -300,6 +328,7 @@ static rfnse_status solve_mixed(rfnse_ctx* c, const double* D, const double2* f,
     beta = pk.beta;
     if (!std::isfinite(beta)) { c->err = "non-finite residual"; return RFNSE_ENUMERIC; }
     r = c->r;
+    c->resid_current = true;
   }
   *iters = it;
   *outer_out = outer;
@@ -310,6 +339,7 @@ rfnse_status solve_block(rfnse_ctx* c, const double* D, const double2* f, double
                          double* relres) {
   int outer = 0;
   rfnse_status st;
+  RFNSE_CUDA_TRY(c, prepare_D(c, D));
   if (c->p.precision == 1) {
     st = solve_mixed(c, D, f, x, half, iters, relres, &outer);
   } else {
@@ -323,12 +353,23 @@ rfnse_status solve_block(rfnse_ctx* c, const double* D, const double2* f, double
 // ---------------------------------------------------------------------------------------------
 // Time steps (paper Sec. 2.1/2.2): (D - T + iI) u^{n+1} = (T - D + iI) u^{n-1}, solved in the
 // block form R x = f with f = -i b = u^{n-1} - i (T - D) u^{n-1}.
+//
+// Mixed form: the final FP64 residual of each solve gives T u^{n+1} pointwise (kept in c->Tu), so
+// the right-hand side of step n+2, which needs T u^{n+1}, costs no Toeplitz product.
+static void keep_Tu(rfnse_ctx* c, rfnse_status st, const double* D, const double2* f, int inext, double scale) {
+  if (c->Tu[inext] && st == RFNSE_OK && c->p.precision == 1 && c->resid_current) {
+    launch_tu_from_residual(D, f, c->u[inext], c->r, c->Tu[inext], scale, c->N, c->stream);
+    c->tu_valid[inext] = true;
+  }
+}
+
 rfnse_status time_step(rfnse_ctx* c, int* iters, double* relres) {
   const long long N = c->N;
   const int inext = 3 - c->iprev - c->icur;
   double2* un = c->u[inext];
   rfnse_status st = RFNSE_OK, st2;
   int it = 0;
+  c->tu_valid[inext] = false;
   if (c->step == 0) {
     const double2* u0 = c->u[c->icur];
     const double rdt = c->p.rho * c->p.dt * 0.5;
@@ -345,13 +386,19 @@ rfnse_status time_step(rfnse_ctx* c, int* iters, double* relres) {
       if (st2 != RFNSE_OK) st = st2;
       it += it2;
     }
+    keep_Tu(c, st, c->D, c->f, inext, 2.0);  // the first step's system has T/2
   } else {
     const double2* up = c->u[c->iprev];
     const double2* uc = c->u[c->icur];
     launch_diag(uc, nullptr, c->D, c->p.rho * c->p.dt, N, c->stream);
-    RFNSE_CUDA_TRY(c, run_matvec_fp64(c, up, c->D, c->f, nullptr, kOne, kMinusI, 0));
+    if (c->tu_valid[c->iprev]) {
+      launch_rhs_from_tu(up, c->Tu[c->iprev], c->D, c->f, N, c->stream);
+    } else {
+      RFNSE_CUDA_TRY(c, run_matvec_fp64(c, up, c->D, c->f, nullptr, kOne, kMinusI, 0));
+    }
     st = solve_block(c, c->D, c->f, un, 0, &it, relres);
     if (st != RFNSE_OK && st != RFNSE_ENOCONV) return st;
+    keep_Tu(c, st, c->D, c->f, inext, 1.0);
   }
   c->iprev = c->icur;
   c->icur = inext;
