@@ -55,7 +55,10 @@ struct PassParams {
   const void* circ;        // circulant eigenvalues of this axis times mu_a / L (length L), compute precision
   double dst_scale;        // 1/sqrt(2(n+1))
   double2 ca, cb;          // epilogue scalars a and b
+  float dst_scale_f;       // the same in FP32 (set by launch_pass): FP32 kernels convert nothing
+  float2 ca_f, cb_f;
   int n, L, log2L, nt, B;  // axis extent, FFT length, log2 L, threads per line, lines per block
+  int log2B;               // B = 2^log2B
   long long stride;        // element stride of the axis
   long long nlines;        // N / n
   long long tiles_inner;   // strided axes: ceil(stride / B)
@@ -83,6 +86,8 @@ __global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
   const bool xax = (p.stride == 1);
   const V zero = cvec<R>::make((R)0, (R)0);
 
+  for (int i = tid; i < L; i += nthr) tws[i] = ld_c<R>(p.tw, i);
+
   long long line0 = 0, hi = 0, lo0 = 0;
   if (xax) {
     line0 = (long long)blockIdx.x * B;
@@ -91,9 +96,16 @@ __global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
     lo0 = ((long long)blockIdx.x - hi * p.tiles_inner) * B;
   }
   // element e of the tile -> (line l, position pos), ordered for coalesced global access
+  // (B is a power of two; a tile of x-lines of the large transforms is a single line)
+  const int log2B = p.log2B;
   auto map = [&](int e, int& l, int& pos) {
-    if (xax) { l = e / n; pos = e - l * n; }
-    else { pos = e / B; l = e - pos * B; }
+    if (xax) {
+      if (B == 1) { l = 0; pos = e; }
+      else { l = e / n; pos = e - l * n; }
+    } else {
+      pos = e >> log2B;
+      l = e & (B - 1);
+    }
   };
   auto gidx = [&](int l, int pos, bool& valid) -> long long {
     if (xax) {
@@ -108,7 +120,6 @@ __global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
   auto at = [&](int l, int i) -> V& { return buf[(size_t)l * Lp + fft_pad(i)]; };
 
   // ---- load -----------------------------------------------------------------------------------
-  for (int i = tid; i < L; i += nthr) tws[i] = ld_c<R>(p.tw, i);
   const TIN* in = reinterpret_cast<const TIN*>(p.in);
   double sc = 1.0;
   if (FLAGS & F_INSCALE) sc = *p.in_scale;
@@ -148,7 +159,7 @@ __global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
   }
   __syncthreads();
 
-  const R dsc = (R)p.dst_scale;
+  const R dsc = sizeof(R) == 4 ? (R)p.dst_scale_f : (R)p.dst_scale;
 
   // ---- sine transforms ------------------------------------------------------------------------
   if (FLAGS & F_DST) {
@@ -219,7 +230,8 @@ __global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
 
   // ---- Toeplitz product by circulant embedding ------------------------------------------------
   if (FLAGS & (F_TOEP_X | F_TOEP_ACC)) {
-    fft_lines(buf, Lp, L, p.log2L, p.nt, tws, false);
+    // the embedded vector is zero from position L/2 on, and only positions 1..n < L/2 are read back
+    fft_lines(buf, Lp, L, p.log2L, p.nt, tws, false, /*zero_upper=*/true, false);
     const R* circ = reinterpret_cast<const R*>(p.circ);
     for (int e = tid; e < B * L; e += nthr) {
       const int l = e >> p.log2L;
@@ -227,8 +239,9 @@ __global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
       at(l, k) = cscale(at(l, k), circ[k]);
     }
     __syncthreads();
-    fft_lines(buf, Lp, L, p.log2L, p.nt, tws, true);
-    const V ca = cvec<R>::make((R)p.ca.x, (R)p.ca.y), cb = cvec<R>::make((R)p.cb.x, (R)p.cb.y);
+    fft_lines(buf, Lp, L, p.log2L, p.nt, tws, true, false, /*half_out=*/true);
+    const V ca = sizeof(R) == 4 ? cvec<R>::make((R)p.ca_f.x, (R)p.ca_f.y) : cvec<R>::make((R)p.ca.x, (R)p.ca.y);
+    const V cb = sizeof(R) == 4 ? cvec<R>::make((R)p.cb_f.x, (R)p.cb_f.y) : cvec<R>::make((R)p.cb.x, (R)p.cb.y);
     const TACCI* accin = reinterpret_cast<const TACCI*>(p.acc_in);
     TACCO* accout = reinterpret_cast<TACCO*>(p.acc_out);
     const R* Dr = reinterpret_cast<const R*>(p.Dr);
@@ -260,8 +273,7 @@ inline void pass_geometry(int L, bool xax, long long lines_avail, int& nt, int& 
   if (nt > target) target = nt;
   B = target / nt;
   if (B < 1) B = 1;
-  if (B > lines_avail) B = (int)lines_avail;
-  if (B < 1) B = 1;
+  while (B > 1 && B > lines_avail) B >>= 1;  // keep B a power of two
 }
 
 // Algorithmic work of one launch: 5 L log2 L flops per complex FFT of length L per line, and
@@ -288,6 +300,11 @@ cudaError_t launch_pass(rfnse_ctx* c, PassParams p, cudaStream_t s) {
   using V = cv<R>;
   const bool xax = (p.stride == 1);
   pass_geometry(p.L, xax, xax ? p.nlines : p.stride, p.nt, p.B);
+  p.dst_scale_f = (float)p.dst_scale;
+  p.ca_f = make_float2((float)p.ca.x, (float)p.ca.y);
+  p.cb_f = make_float2((float)p.cb.x, (float)p.cb.y);
+  p.log2B = 0;
+  while ((1 << p.log2B) < p.B) ++p.log2B;
   long long grid;
   if (xax) {
     grid = (p.nlines + p.B - 1) / p.B;

@@ -25,7 +25,7 @@ __global__ void k_coefficients(double* c, int nmax, double alpha) {
 //     leading n x n block;
 //   lam[k-1] = circ[k], k = 1..n: the eigenvalues of tau(T_0) = T_0 - HC(T_0) (eq. 'taudefine',
 //     'taudiagonal'), i.e. c_0 + 2 sum_m c_m cos(pi m k/(n+1)).
-//   tw[k] = exp(-2 pi i k / L).
+//   tw: the per-stage twiddle table of a length-L FFT (layout in fft_line.cuh), FP64 and FP32.
 __global__ void k_axis_tables(const double* __restrict__ c, int n, int L, double* __restrict__ lam,
                               double* __restrict__ circ, double2* __restrict__ tw64, float2* __restrict__ tw32) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -39,8 +39,21 @@ __global__ void k_axis_tables(const double* __restrict__ c, int n, int L, double
   const double v = c[0] + 2.0 * s;
   circ[k] = v;
   if (k >= 1 && k <= n) lam[k - 1] = v;
-  double sn, cs;
-  sincospi(2.0 * (double)k / (double)L, &sn, &cs);
+  // twiddle entry k of the per-stage table of fft_line.cuh: stage Ns holds W_{4Ns}^{r kk},
+  // r = 1..3, kk = 0..Ns-1, at (r-1) Ns + kk of its segment
+  int log2L = 0;
+  while ((1 << log2L) < L) ++log2L;
+  int t = k, Ns = (log2L & 1) ? 2 : 4;
+  while (Ns < L && t >= 3 * Ns) {
+    t -= 3 * Ns;
+    Ns <<= 2;
+  }
+  double sn = 0.0, cs = 1.0;
+  if (Ns < L) {
+    const int r = t / Ns + 1, kk = t - (r - 1) * Ns;
+    // exp(-2 pi i r kk / (4 Ns)) = exp(-i pi (r kk)/(2 Ns)); the argument is an exact binary fraction
+    sincospi((double)(r * kk) / (double)(2 * Ns), &sn, &cs);
+  }
   tw64[k] = make_double2(cs, -sn);
   tw32[k] = make_float2((float)cs, (float)-sn);
 }

@@ -246,6 +246,30 @@ def test_config_1d_full_trajectory_fp64():
         assert abs(int(iters[k]) - its_ref[k]) <= 1
 
 
+@pytest.mark.parametrize("precision", (1, 0))
+def test_config_3d_255_steps_solve_the_printed_system(precision):
+    """d=3, n=255^3, alpha=1.7, rho=1, dt=0.01, tol 1e-8 (full size; the oracle cannot run whole
+    trajectories here in test time).  Property check with the oracle's own operators: the GPU's u^2
+    solves (D - T + iI) u^2 = (T - D + iI) u^0 with D = rho dt |u^1|^2 to the tolerance, and
+    ||u^2|| = ||u^0|| (the scheme is a Cayley transform)."""
+    p, u0, _ = W.config_3d()
+    s = Solver(p, precision=precision)
+    s.set_state(dev(u0))
+    traj = torch.empty(2 * p.size, dtype=torch.complex128, device="cuda")
+    iters, relres = s.run(2, traj)
+    s.close()
+    u = traj.cpu().numpy().reshape((2,) + p.shape)
+    del traj
+    u1, u2 = u[0], u[1]
+    T = ToeplitzOperator(p)
+    D = diag_D(u1, p.rho, p.dt)
+    b = T(u0) - D * u0 + 1j * u0
+    res = D * u2 - T(u2) + 1j * u2 - b
+    assert np.linalg.norm(res) / np.linalg.norm(b) < 2 * p.tol
+    assert abs(np.linalg.norm(u2) - np.linalg.norm(u0)) < 1e-7 * np.linalg.norm(u0)
+    assert 1 <= iters[1] <= 20
+
+
 @pytest.mark.parametrize("alpha", W.CONFIG_2D_ALPHAS)
 @pytest.mark.parametrize("precision", (0, 1))
 def test_config_2d_511_first_steps(alpha, precision):
