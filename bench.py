@@ -36,6 +36,8 @@ import workloads as W  # noqa: E402
 METRIC = "DOF*timesteps/s"
 UNIT = "DOF*timesteps/s"
 FP64_ALU_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP64 Toeplitz x-pass (ncu)
+TRAFFIC_FP64_TOEP_X = {"2d": 10530816 + 0}
 
 
 def parse():
@@ -49,6 +51,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--serial", action="store_true", help="advance the instances one after another on one stream")
+    ap.add_argument("--alu-probe", action="store_true",
+                    help="only measure the FP64 and FP32 FMA rates of the GPU and print them")
     return ap.parse_args()
 
 
@@ -241,11 +245,11 @@ def run_ours(args):
     concurrent = not args.serial and len(inst) > 1
     pool = ThreadPoolExecutor(max_workers=len(inst)) if concurrent else None
 
-    def make(precision):
+    def make(precision, device_loop=1):
         solvers = []
         for p, u0 in inst:
             st = torch.cuda.Stream(device=dev) if concurrent else main
-            s = rfnse.Solver(p, precision=precision, stream=st)
+            s = rfnse.Solver(p, precision=precision, stream=st, device_loop=device_loop)
             s.set_state(torch.from_numpy(u0.ravel().copy()).to(dev))
             solvers.append(s)
         torch.cuda.synchronize()
@@ -316,7 +320,13 @@ def run_ours(args):
     mixed_states = [s.get_state()[1] for s in mixed]   # after warmup + steps, for the FP64 comparison
     # the dominant kernel class, timed launch by launch in a further serial run of the same steps
     # (in the concurrent region the instances' kernels share the SMs, which stretches each launch)
-    ms_r, _, _, _, prof = timed(mixed, max(1, min(args.steps, 20)), 0, profile_kind=dom_kind, serial=True)
+    # (host-driven solvers: CUDA events cannot be recorded around single kernels inside a running graph;
+    # the kernels are the same as in the device loop)
+    prof_solvers = make(1, device_loop=0)
+    ms_r, _, _, _, prof = timed(prof_solvers, max(1, min(args.steps, 20)), args.warmup, profile_kind=dom_kind,
+                                serial=True)
+    for s in prof_solvers:
+        s.close()
     ms_max = reduce_max(ms, world, dev)
     value = world * dof_per_step * args.steps / (ms_max * 1e-3)
 
@@ -339,7 +349,10 @@ def run_ours(args):
         peak = FP64_ALU_PEAK_FLOPS / 1e12
         out["roofline"] = {"bound": "alu", "kernel": "k_line_pass<double,F_TOEP_X> (FP64 Toeplitz x-pass)",
                            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                           "traffic": None, "launches": n, "avg_launch_us": 1e3 * pms / n,
+                           # DRAM read+write of one launch of this kernel, ncu capture of the current
+                           # code on the 2-D 511^2 workload (profiles/k_line_pass_fp64_toeplitz_x_2d511.md)
+                           "traffic": TRAFFIC_FP64_TOEP_X.get(args.workload), "launches": n,
+                           "avg_launch_us": 1e3 * pms / n,
                            "share_of_step_time": pms / ms_r if ms_r > 0 else None,
                            "measured": "CUDA events around every launch of the class, serial run of "
                                        f"{max(1, min(args.steps, 20))} further bench steps",
@@ -420,8 +433,22 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def alu_probe():
+    import torch
+    from paper_2410_03643_gb300 import build, rfnse
+    build.build_library()
+    props = torch.cuda.get_device_properties(0)
+    out = {"device": props.name, "sms": props.multi_processor_count,
+           "fp64_tflops": rfnse.probe_fma(True) / 1e12, "fp32_tflops": rfnse.probe_fma(False) / 1e12}
+    out["fp32_over_fp64"] = out["fp32_tflops"] / out["fp64_tflops"]
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.alu_probe:
+        alu_probe()
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

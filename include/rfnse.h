@@ -60,10 +60,12 @@ typedef struct {
   int first_step;     /* 0 = predictor only, 1 = predictor-corrector Crank-Nicolson first step */
   double inner_tol;   /* mixed form: relative tolerance of each inner solve (<= 0: 1e-6) */
   int max_outer;      /* mixed form: maximum refinement steps per solve (<= 0: 30) */
+  int device_loop;    /* 1 = each solve is one CUDA graph whose conditional loops are decided on the
+                         device (no host round trip per Arnoldi step); 0 = host-driven loop */
 } rfnse_params;
 
 /* Fill p with defaults: d=1, n=255, box [-20,20], alpha=1.5, rho=2, dt=0.01, omega=1, restart=20,
-   max_it=2000, tol=1e-10, precision=0, first_step=1, inner_tol=1e-6, max_outer=30. */
+   max_it=2000, tol=1e-10, precision=0, first_step=1, inner_tol=1e-6, max_outer=30, device_loop=1. */
 void rfnse_default_params(rfnse_params* p);
 
 /* Create a solver context for the problem p (Sec. 2: grid, alpha, rho, dt) on the current CUDA
@@ -163,6 +165,12 @@ int rfnse_apply_prec_static(const rfnse_params* p, const void* v, void* z, const
 
 /* Number of CUDA kernels this library has launched in the calling process (all contexts). */
 long long rfnse_launch_count(void);
+
+/* Measure the FMA throughput of the current device (flop/s, 2 flops per FMA) in FP64 (fp64 = 1) or
+   FP32 (fp64 = 0) with independent FMA chains on 8 blocks of 256 threads per SM, timed with CUDA
+   events on the legacy default stream.  Allocates and frees a small device buffer.  Used to confirm
+   the FP64 arithmetic peak that bounds the FP64 line passes.  Errors: EINVAL, ENOMEM, ECUDA. */
+int rfnse_probe_fma(int fp64, double* flops_per_s);
 
 /* Kernel classes of rfnse_profile: OR of the operations a line pass fuses, plus RFNSE_K_FP32 for
    passes computing in FP32.  RFNSE_K_INSCALE is ignored when matching. */

@@ -65,6 +65,14 @@ void free_ctx(rfnse_ctx* c) {
   cudaFree(c->gs);
   if (c->peek) cudaFreeHost(c->peek);
   for (cudaEvent_t ev : c->prof_events) cudaEventDestroy(ev);
+  for (int a = 0; a < 2; ++a)
+    for (int h = 0; h < 2; ++h) {
+      if (c->graph_exec[a][h]) cudaGraphExecDestroy(c->graph_exec[a][h]);
+      if (c->graph[a][h]) cudaGraphDestroy(c->graph[a][h]);
+    }
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  cudaFree(c->bar);
+  cudaFree(c->coop_partials);
   delete c;
 }
 
@@ -114,6 +122,7 @@ void rfnse_default_params(rfnse_params* p) {
   p->first_step = 1;
   p->inner_tol = 1e-6;
   p->max_outer = 30;
+  p->device_loop = 1;
 }
 
 int rfnse_create(const rfnse_params* p, void* stream, rfnse_ctx** out) {
@@ -188,6 +197,11 @@ int rfnse_create(const rfnse_params* p, void* stream, rfnse_ctx** out) {
     }
   }
   c->red_blocks = choose_reduce_blocks(N);
+  c->use_graphs = p->device_loop != 0;
+  c->coop_blocks = coop_blocks_for(N);
+  chk(dalloc(&c->bar, 1));
+  chk(dalloc(&c->coop_partials, 2 * (size_t)c->coop_blocks));
+  if (e == cudaSuccess) chk(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   chk(dalloc(&c->partials, 1024));
   chk(dalloc(&c->counter, 1));
   chk(dalloc(&c->gs, 1));
@@ -200,6 +214,7 @@ int rfnse_create(const rfnse_params* p, void* stream, rfnse_ctx** out) {
   }
   chk(cudaMemsetAsync(c->counter, 0, sizeof(unsigned), c->stream));
   chk(cudaMemsetAsync(c->gs, 0, sizeof(GmresState), c->stream));
+  chk(cudaMemsetAsync(c->bar, 0, sizeof(GridBarrier), c->stream));
   chk(cudaMemsetAsync(c->u[0], 0, sizeof(double2) * N, c->stream));
   chk(cudaMemsetAsync(c->u[1], 0, sizeof(double2) * N, c->stream));
   launch_setup_coefficients(c->c, nmax, p->alpha, c->stream);

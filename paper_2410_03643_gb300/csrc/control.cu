@@ -1,0 +1,348 @@
+// Device-side control of the GMRES solve (paper Sec. 5, "PGMRES"): the Arnoldi step with modified
+// Gram-Schmidt, Givens rotations and the convergence test in one cooperative kernel, and the small
+// kernels that start a solve or a cycle and decide, on the device, whether the next Arnoldi step,
+// restart or refinement cycle runs.  With a CUDA graph whose conditional WHILE nodes read the
+// handles these kernels set, a whole solve runs without the host.
+#include <cmath>
+#include "internal.cuh"
+
+namespace rfnse {
+
+constexpr int kCtlThreads = 256;
+constexpr unsigned long long kMaxSpin = 1ull << 22;  // bounded barrier wait (~0.3 s), then err = 1
+
+__device__ __forceinline__ double block_sum_c(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+  if (warp == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  return v;  // valid in thread 0
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).  The wait is bounded: after
+// kMaxSpin polls the block records the failure in *err and continues.
+__device__ __forceinline__ void grid_barrier(GridBarrier* b, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &b->gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&b->count, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(&b->count, 0u);
+      __threadfence();
+      atomicAdd(&b->gen, 1u);
+    } else {
+      unsigned long long spins = 0;
+      while (*vgen == g) {
+        if (++spins > kMaxSpin) {
+          *(volatile int*)err = 1;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// The same value in every block: the partials summed in a fixed order.
+__device__ __forceinline__ double fixed_sum(const double* part, int n, double* sh) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += ((volatile const double*)part)[i];
+  v = block_sum_c(v, sh);
+  __shared__ double bc;
+  if (threadIdx.x == 0) bc = v;
+  __syncthreads();
+  return bc;
+}
+
+// Arnoldi step j = gs->j: w holds A M^{-1} v_j.  Modified Gram-Schmidt (for i = 0..j:
+// h_ij = <v_i, w>, w -= h_ij v_i; one pass per i fusing the previous subtraction with the next dot),
+// h_{j+1,j} = ||w||, the Givens update of column j and the convergence test; then the state for the
+// next column (src = w, scale = 1/h_{j+1,j}, j + 1) and, if set_cond, the inner-loop condition.
+__global__ void __launch_bounds__(kCtlThreads) k_mgs_step(GmresState* gs, const double2* __restrict__ V,
+                                                         long long ldv, double2* __restrict__ w, long long N,
+                                                         double* partials, GridBarrier* bar, SolveCfg cfg,
+                                                         cudaGraphConditionalHandle h_inner, int set_cond) {
+  __shared__ double sh[32];
+  const int j = gs->j;
+  const int nb = gridDim.x;
+  double hprev = 0.0;
+  double nrm2 = 0.0;
+  for (int i = 0; i <= j + 1; ++i) {
+    double* buf = partials + (size_t)(i & 1) * nb;
+    const double2* vi = (i <= j) ? V + (size_t)i * ldv : nullptr;
+    const double2* vp = (i > 0) ? V + (size_t)(i - 1) * ldv : nullptr;
+    double acc = 0.0;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (long long)nb * blockDim.x) {
+      double2 wv = w[k];
+      if (vp) {
+        const double2 pv = vp[k];
+        wv.x -= hprev * pv.x;
+        wv.y -= hprev * pv.y;
+        w[k] = wv;
+      }
+      if (vi) {
+        const double2 a = vi[k];
+        acc += a.x * wv.x + a.y * wv.y;
+      } else {
+        acc += wv.x * wv.x + wv.y * wv.y;
+      }
+    }
+    acc = block_sum_c(acc, sh);
+    if (threadIdx.x == 0) buf[blockIdx.x] = acc;
+    __threadfence();
+    grid_barrier(bar, &gs->err);
+    const double s = fixed_sum(buf, nb, sh);
+    if (i <= j) {
+      hprev = s;
+      if (blockIdx.x == 0 && threadIdx.x == 0) gs->H[(size_t)j * (kMaxM + 1) + i] = s;
+    } else {
+      nrm2 = s;
+    }
+  }
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  double* Hc = gs->H + (size_t)j * (kMaxM + 1);
+  const double hnext = sqrt(nrm2);
+  Hc[j + 1] = hnext;
+  for (int i = 0; i < j; ++i) {  // previous rotations
+    const double t = gs->cs[i] * Hc[i] + gs->sn[i] * Hc[i + 1];
+    Hc[i + 1] = -gs->sn[i] * Hc[i] + gs->cs[i] * Hc[i + 1];
+    Hc[i] = t;
+  }
+  const double rr = hypot(Hc[j], Hc[j + 1]);
+  const double c = Hc[j] / rr, sn = Hc[j + 1] / rr;
+  gs->cs[j] = c;
+  gs->sn[j] = sn;
+  Hc[j] = rr;
+  Hc[j + 1] = 0.0;
+  gs->g[j + 1] = -sn * gs->g[j];
+  gs->g[j] = c * gs->g[j];
+  const double rel = fabs(gs->g[j + 1]) / gs->ref;
+  gs->relres = rel;
+  gs->inv_h = (hnext > 0.0) ? 1.0 / hnext : 0.0;
+  int done = 0;
+  if (!isfinite(rel) || !isfinite(hnext)) done = 3;
+  else if (rel < gs->tol) done = 1;
+  else if (hnext == 0.0) done = 2;
+  gs->done = done;
+  gs->it += 1;
+  gs->j = j + 1;
+  gs->src = w;
+  gs->src_scale = gs->inv_h;
+  const int stop = done != 0 || gs->it >= cfg.max_it || gs->err;
+  gs->no_restart = stop;
+  if (set_cond) cudaGraphSetConditional(h_inner, (!stop && j + 1 < cfg.m) ? 1u : 0u);
+}
+
+// ||x|| into gs (beta, 1/beta, g = beta e_1), fixed-order reduction; then, by mode:
+//   mode 0 (solve start): fnorm = beta, src = x (= f), it = outer = j = err = 0; outer condition = beta > 0
+//   mode 1 (FP64 restart): skipped when gs->no_restart (outer condition 0); else relres = beta/fnorm,
+//          converged -> done = 1; outer condition = not converged
+//   mode 2 (mixed refinement): outer += 1; relres = beta/fnorm; outer condition = beta/fnorm >= tol and
+//          outer < max_outer and it < max_it
+// In modes 1, 2 the new cycle starts from src = x (= r) with scale 1/beta.
+__global__ void __launch_bounds__(kCtlThreads) k_norm_ctl(const double2* __restrict__ x, GmresState* gs, long long N,
+                                                         double* partials, unsigned* counter, GridBarrier* bar,
+                                                         SolveCfg cfg, int mode, cudaGraphConditionalHandle h_outer,
+                                                         int set_cond) {
+  __shared__ double sh[32];
+  __shared__ bool last;
+  if (mode == 1 && gs->no_restart) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && set_cond) cudaGraphSetConditional(h_outer, 0u);
+    return;
+  }
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = x[i];
+    acc += v.x * v.x + v.y * v.y;
+  }
+  acc = block_sum_c(acc, sh);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = acc;
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += ((volatile const double*)partials)[i];
+  s = block_sum_c(s, sh);
+  if (threadIdx.x != 0) return;
+  *counter = 0u;
+  const double b = sqrt(s);
+  gs->beta = b;
+  gs->inv_beta = (b > 0.0) ? 1.0 / b : 0.0;
+  gs->g[0] = b;
+  for (int i = 1; i <= kMaxM; ++i) gs->g[i] = 0.0;
+  gs->src = x;
+  gs->src_scale = gs->inv_beta;
+  gs->j = 0;
+  unsigned cont;
+  if (mode == 0) {
+    gs->fnorm = b;
+    gs->it = 0;
+    gs->outer = 0;
+    gs->err = 0;
+    gs->no_restart = 0;
+    gs->done = isfinite(b) ? 0 : 3;
+    gs->relres = (b > 0.0) ? 1.0 : 0.0;
+    bar->count = 0u;
+    cont = (b > 0.0 && isfinite(b)) ? 1u : 0u;
+  } else {
+    gs->outer += 1;
+    const double rel = b / gs->fnorm;
+    gs->relres = rel;
+    if (!isfinite(b)) {
+      gs->done = 3;
+      cont = 0u;
+    } else if (rel < cfg.tol) {
+      gs->done = 1;
+      cont = 0u;
+    } else {
+      gs->done = 0;
+      cont = (mode == 1) ? 1u : ((gs->outer < cfg.max_outer && gs->it < cfg.max_it && !gs->err) ? 1u : 0u);
+    }
+  }
+  if (set_cond) cudaGraphSetConditional(h_outer, cont);
+}
+
+// Start of an Arnoldi cycle: reference norm and tolerance of the relative residual test, j = 0, and
+// the inner-loop condition set to run.  FP64 form: ref = ||f||, tol = tol.  Mixed form: ref = beta
+// (the outer residual), tol = max(eta_min, 0.1 tol ||f|| / beta).
+// The outer condition is cleared here and set again only by the residual kernel at the end of the
+// cycle, so the outer loop can only stop early if that kernel does not run.
+__global__ void k_cycle_begin(GmresState* gs, SolveCfg cfg, cudaGraphConditionalHandle h_inner,
+                              cudaGraphConditionalHandle h_outer, int set_cond) {
+  if (cfg.mixed) {
+    gs->ref = gs->beta;
+    gs->tol = fmax(cfg.eta_min, 0.1 * cfg.tol * gs->fnorm / gs->beta);
+  } else {
+    gs->ref = gs->fnorm;
+    gs->tol = cfg.tol;
+  }
+  gs->j = 0;
+  gs->done = 0;
+  gs->no_restart = 0;
+  if (set_cond) {
+    cudaGraphSetConditional(h_outer, 0u);
+    cudaGraphSetConditional(h_inner, 1u);
+  }
+}
+
+// y = R^{-1} g on the leading k x k triangle, k = gs->j (single thread).
+__global__ void k_backsolve_dev(GmresState* gs) {
+  const int k = gs->j;
+  const int ld = kMaxM + 1;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = gs->g[i];
+    for (int jj = i + 1; jj < k; ++jj) s -= gs->H[(size_t)jj * ld + i] * gs->y[jj];
+    gs->y[i] = s / gs->H[(size_t)i * ld + i];
+  }
+}
+
+// out = sum_{i<k} y_i V_i, k = gs->j
+__global__ void k_combine_dev(const double2* __restrict__ V, long long ldv, const GmresState* gs,
+                              double2* __restrict__ out, long long N) {
+  __shared__ double y[kMaxM];
+  const int k = gs->j;
+  if (threadIdx.x < k) y[threadIdx.x] = gs->y[threadIdx.x];
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    double2 a = make_double2(0.0, 0.0);
+    for (int q = 0; q < k; ++q) {
+      const double2 v = V[(size_t)q * ldv + i];
+      a.x += y[q] * v.x;
+      a.y += y[q] * v.y;
+    }
+    out[i] = a;
+  }
+}
+
+// x += sum_{i<k} y_i Z_i (Z in FP32), k = gs->j
+__global__ void k_combine_f32_add_dev(const float2* __restrict__ Z, long long ldz, const GmresState* gs,
+                                      double2* __restrict__ x, long long N) {
+  __shared__ double y[kMaxM];
+  const int k = gs->j;
+  if (threadIdx.x < k) y[threadIdx.x] = gs->y[threadIdx.x];
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    double2 a = x[i];
+    for (int q = 0; q < k; ++q) {
+      const float2 v = Z[(size_t)q * ldz + i];
+      a.x += y[q] * (double)v.x;
+      a.y += y[q] * (double)v.y;
+    }
+    x[i] = a;
+  }
+}
+
+static inline unsigned ew_blocks_c(long long N) {
+  long long b = (N + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+int coop_blocks_for(long long N) {
+  int dev = 0, sms = 152, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mgs_step, kCtlThreads, 0);
+  long long b = (long long)sms * (per_sm < 2 ? per_sm : 2);
+  const long long need = (N + kCtlThreads - 1) / kCtlThreads;
+  if (b > need) b = need;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+cudaError_t launch_mgs_step(GmresState* gs, const double2* V, long long ldv, double2* w, long long N,
+                            double* partials, GridBarrier* bar, const SolveCfg& cfg,
+                            cudaGraphConditionalHandle h_inner, int set_cond, int blocks, cudaStream_t s) {
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)blocks);
+  lc.blockDim = dim3(kCtlThreads);
+  lc.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  count_launch();
+  return cudaLaunchKernelEx(&lc, k_mgs_step, gs, V, ldv, w, N, partials, bar, cfg, h_inner, set_cond);
+}
+
+void launch_norm_ctl(const double2* x, GmresState* gs, long long N, int blocks, double* partials, unsigned* counter,
+                     GridBarrier* bar, const SolveCfg& cfg, int mode, cudaGraphConditionalHandle h_outer,
+                     int set_cond, cudaStream_t s) {
+  count_launch();
+  k_norm_ctl<<<blocks, kCtlThreads, 0, s>>>(x, gs, N, partials, counter, bar, cfg, mode, h_outer, set_cond);
+}
+void launch_cycle_begin(GmresState* gs, const SolveCfg& cfg, cudaGraphConditionalHandle h_inner,
+                        cudaGraphConditionalHandle h_outer, int set_cond, cudaStream_t s) {
+  count_launch();
+  k_cycle_begin<<<1, 1, 0, s>>>(gs, cfg, h_inner, h_outer, set_cond);
+}
+void launch_backsolve_dev(GmresState* gs, cudaStream_t s) {
+  count_launch();
+  k_backsolve_dev<<<1, 1, 0, s>>>(gs);
+}
+void launch_combine_dev(const double2* V, long long ldv, const GmresState* gs, double2* out, long long N,
+                        cudaStream_t s) {
+  count_launch();
+  k_combine_dev<<<ew_blocks_c(N), 256, 0, s>>>(V, ldv, gs, out, N);
+}
+void launch_combine_f32_add_dev(const float2* Z, long long ldz, const GmresState* gs, double2* x, long long N,
+                                cudaStream_t s) {
+  count_launch();
+  k_combine_f32_add_dev<<<ew_blocks_c(N), 256, 0, s>>>(Z, ldz, gs, x, N);
+}
+
+}  // namespace rfnse

@@ -24,11 +24,20 @@ struct GmresState {
   double relres;    // |g_{j+1}| / ref after the last Givens update
   int done;         // 0 running, 1 converged, 2 exact breakdown, 3 non-finite value
   int pad_;
+  int it;           // Arnoldi steps of the current solve
+  int outer;        // outer (restart / refinement) cycles of the current solve
+  int err;          // 1: a bounded device-side wait gave up
+  int j;            // next Arnoldi column of the cycle (= columns built so far)
   // --- device-only ---
   double inv_beta;  // 1 / beta
   double ref;       // reference norm of the relative residual test
   double tol;       // stop when |g_{j+1}| / ref < tol
   double inv_h;     // 1 / h_{j+1,j}
+  double fnorm;     // ||f|| of the solve
+  const double2* src;  // vector that starts the next Arnoldi column (r or w) ...
+  double src_scale;    // ... and the factor that normalises it (1/beta or 1/h)
+  int no_restart;   // 1 when the cycle ended converged or out of iterations (restart kernels skip)
+  int pad2_;
   double H[(kMaxM + 1) * kMaxM];
   double cs[kMaxM], sn[kMaxM], g[kMaxM + 1], y[kMaxM];
 };
@@ -37,7 +46,40 @@ struct GmresState {
 struct GmresPeek {
   double beta, relres;
   int done, pad_;
+  int it, outer, err, j;
 };
+
+// Settings of a solve that the device-side control reads.
+struct SolveCfg {
+  int m;            // restart length
+  int max_it;       // Arnoldi steps per solve
+  int max_outer;    // refinement cycles (mixed form)
+  int mixed;        // 1: mixed form (inner tolerance from eta_min, FP64 outer residual)
+  double tol;       // relative residual tolerance of the solve
+  double eta_min;   // mixed form: smallest inner tolerance
+};
+
+// Counter and generation of a grid-wide barrier (control.cu); zero-initialised.
+struct GridBarrier {
+  unsigned count;
+  unsigned gen;
+};
+
+// ---- device-side control (control.cu) -----------------------------------------------------------
+int coop_blocks_for(long long N);  // blocks of the cooperative Arnoldi kernel (all co-resident)
+cudaError_t launch_mgs_step(GmresState* gs, const double2* V, long long ldv, double2* w, long long N,
+                            double* partials, GridBarrier* bar, const SolveCfg& cfg,
+                            cudaGraphConditionalHandle h_inner, int set_cond, int blocks, cudaStream_t s);
+void launch_norm_ctl(const double2* x, GmresState* gs, long long N, int blocks, double* partials, unsigned* counter,
+                     GridBarrier* bar, const SolveCfg& cfg, int mode, cudaGraphConditionalHandle h_outer,
+                     int set_cond, cudaStream_t s);
+void launch_cycle_begin(GmresState* gs, const SolveCfg& cfg, cudaGraphConditionalHandle h_inner,
+                        cudaGraphConditionalHandle h_outer, int set_cond, cudaStream_t s);
+void launch_backsolve_dev(GmresState* gs, cudaStream_t s);
+void launch_combine_dev(const double2* V, long long ldv, const GmresState* gs, double2* out, long long N,
+                        cudaStream_t s);
+void launch_combine_f32_add_dev(const float2* Z, long long ldz, const GmresState* gs, double2* x, long long N,
+                                cudaStream_t s);
 
 inline int choose_reduce_blocks(long long N) {
   long long b = (N + 511) / 512;   // enough blocks to cover all 152 SMs; fixed for a given N
@@ -131,6 +173,14 @@ struct rfnse_ctx {
   int red_blocks = 1;
   rfnse::GmresState* gs = nullptr;
   rfnse::GmresPeek* peek = nullptr;  // pinned host
+  // device-side control: cooperative Arnoldi kernel and one CUDA graph per (precision, half)
+  rfnse::GridBarrier* bar = nullptr;
+  double* coop_partials = nullptr;   // 2 * coop_blocks
+  int coop_blocks = 1;
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;  // private stream used only to capture the graphs
+  cudaGraph_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  cudaGraphExec_t graph_exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   // per-step statistics of the last solve
   int last_iters = 0, last_outer = 0;
   double last_relres = 0.0;

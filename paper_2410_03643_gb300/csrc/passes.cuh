@@ -63,6 +63,14 @@ struct PassParams {
   long long nlines;        // N / n
   long long tiles_inner;   // strided axes: ceil(stride / B)
   int z_add;               // F_DSCALE: out += z instead of out = z
+  // device-side control: when gdyn is set, F_INSCALE takes its source vector and factor from the
+  // GMRES state and writes V[j] = vbase + j ldv, and F_DSCALE writes Z[j] = zbase + j ldv (if zbase)
+  const GmresState* gdyn;
+  double2* vbase;
+  void* zbase;
+  long long ldv;
+  const int* skip;         // when set and nonzero, the launch does nothing
+  int in_dyn_z;            // with gdyn: the input is Z[j] = zbase + j ldv (storage TIN)
 };
 
 template <typename R> __device__ __forceinline__ cv<R> ld_c(const void* p, long long i);
@@ -76,6 +84,7 @@ template <> __device__ __forceinline__ float2 ld_c<float>(const void* p, long lo
 template <typename R, typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS>
 __global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
   using V = cv<R>;
+  if (p.skip && *p.skip) return;  // uniform: the whole launch is a no-op
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = p.L, n = p.n, Nh = L >> 1, B = p.B;
   const int Lp = fft_line_stride(L);
@@ -121,8 +130,19 @@ __global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
 
   // ---- load -----------------------------------------------------------------------------------
   const TIN* in = reinterpret_cast<const TIN*>(p.in);
+  if (p.gdyn && p.in_dyn_z) in = reinterpret_cast<const TIN*>(p.zbase) + (long long)p.gdyn->j * p.ldv;
   double sc = 1.0;
-  if (FLAGS & F_INSCALE) sc = *p.in_scale;
+  const double2* src = reinterpret_cast<const double2*>(p.in);
+  double2* cpy = p.copy_out;
+  if (FLAGS & F_INSCALE) {
+    if (p.gdyn) {
+      src = p.gdyn->src;
+      sc = p.gdyn->src_scale;
+      cpy = p.vbase + (long long)p.gdyn->j * p.ldv;
+    } else {
+      sc = *p.in_scale;
+    }
+  }
   for (int e = tid; e < B * n; e += nthr) {
     int l, pos;
     map(e, l, pos);
@@ -131,10 +151,10 @@ __global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
     V v = zero;
     if (valid) {
       if (FLAGS & F_INSCALE) {
-        double2 vd = reinterpret_cast<const double2*>(p.in)[g];
+        double2 vd = src[g];
         vd.x *= sc;
         vd.y *= sc;
-        p.copy_out[g] = vd;
+        cpy[g] = vd;
         v = to_c<R>(vd);
       } else {
         v = to_c<R>(in[g]);
@@ -197,6 +217,7 @@ __global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
   }
   if (FLAGS & F_DSCALE) {
     TOUT* out = reinterpret_cast<TOUT*>(p.out);
+    if (p.gdyn && p.zbase) out = reinterpret_cast<TOUT*>(p.zbase) + (long long)p.gdyn->j * p.ldv;
     for (int e = tid; e < B * n; e += nthr) {
       int l, pos;
       map(e, l, pos);

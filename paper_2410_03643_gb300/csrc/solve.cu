@@ -1,5 +1,12 @@
 // Solver drivers: the preconditioner and matrix sequences of line passes, right-preconditioned
 // GMRES (FP64), the mixed-precision FGMRES with FP64 iterative refinement, and the time steps.
+//
+// Two ways to drive a solve:
+//   * device loop (default): the whole solve is one CUDA graph whose conditional WHILE nodes (outer
+//     restart / refinement cycles, inner Arnoldi steps) are decided by the kernels themselves; the host
+//     launches the graph and reads the statistics once;
+//   * host loop: the host reads the Arnoldi state after every step and launches the next kernels.
+// Both run the same algorithm on the same kernels' arithmetic.
 #include <algorithm>
 #include <cmath>
 #include "internal.cuh"
@@ -51,6 +58,15 @@ cudaError_t prepare_D(rfnse_ctx* c, const double* D) {
   return cudaGetLastError();
 }
 
+// Device-resolved operands of the Arnoldi step (see PassParams::gdyn) and a skip flag.
+struct Dyn {
+  const GmresState* gs = nullptr;
+  double2* vbase = nullptr;
+  void* zbase = nullptr;
+  long long ldv = 0;
+  const int* skip = nullptr;
+};
+
 // ---------------------------------------------------------------------------------------------
 // z = F~^{-1} v (eq. 'taupre'), optionally followed by w = add + a z + b (T - D) z.
 //   R     compute precision of the transforms
@@ -58,45 +74,56 @@ cudaError_t prepare_D(rfnse_ctx* c, const double* D) {
 //   TMP   storage of the intermediate vectors t1, t2
 //   TZ    storage of z
 //   TW    storage of the partial products between Toeplitz passes (w itself when TW = double2)
-// The caller has run prepare_D for D.
+// The caller has run prepare_D for D.  With dyn.gs set, the scaled input, its copy V[j] and (with
+// dyn.zbase) the output Z[j] are resolved on the device.
 template <typename R, typename TIN, typename TMP, typename TZ, typename TW, bool INSC, bool MATVEC>
 cudaError_t run_precon(rfnse_ctx* c, const TIN* v, const double* in_scale, double2* copy_v, TZ* z, int z_add,
                        const double* D, double2* w, TW* wtmp, const double2* w_add, double2 a, double2 b, int half,
-                       TMP* t1, TMP* t2) {
+                       TMP* t1, TMP* t2, const Dyn& dyn = Dyn()) {
   cudaStream_t s = c->stream;
   cudaError_t e;
   constexpr int IS = INSC ? F_INSCALE : 0;
   constexpr int TX = MATVEC ? F_TOEP_X : 0;
   const int h = half ? 1 : 0;
+  auto with_dyn = [&](PassParams& p) {
+    p.gdyn = dyn.gs;
+    p.vbase = dyn.vbase;
+    p.zbase = dyn.zbase;
+    p.ldv = dyn.ldv;
+    p.skip = dyn.skip;
+  };
   if (c->d == 1) {
     PassParams p = base_params<R>(c, 0, h);
     p.in = v; p.in_scale = in_scale; p.copy_out = copy_v; p.out = z; p.z_add = z_add;
     p.Dr = Tables<R>::Dr(c, D); p.dfac = Tables<R>::dfac(c); p.lamfac = Tables<R>::lamfac(c, h);
     p.acc_in = w_add; p.acc_out = w; p.ca = a; p.cb = b;
+    with_dyn(p);
     return launch_pass<R, TIN, TZ, double2, double2, IS | F_DST | F_LAM | F_DSCALE | TX>(c, p, s);
   }
   {  // first axis: forward DST (and the Arnoldi normalisation)
     PassParams p = base_params<R>(c, 0, h);
     p.in = v; p.in_scale = in_scale; p.copy_out = copy_v; p.out = t1;
+    with_dyn(p);
+    p.zbase = nullptr;
     if ((e = launch_pass<R, TIN, TMP, double2, double2, IS | F_DST>(c, p, s)) != cudaSuccess) return e;
   }
   TMP* cur = t1;
   TMP* nxt = t2;
   for (int a2 = 1; a2 < c->d - 1; ++a2) {  // middle axes (d = 3): forward DST
     PassParams p = base_params<R>(c, a2, h);
-    p.in = cur; p.out = nxt;
+    p.in = cur; p.out = nxt; p.skip = dyn.skip;
     if ((e = launch_pass<R, TMP, TMP, double2, double2, F_DST>(c, p, s)) != cudaSuccess) return e;
     std::swap(cur, nxt);
   }
   {  // last axis: DST, multiply by i s/(w + i Lambda), DST
     PassParams p = base_params<R>(c, c->d - 1, h);
-    p.in = cur; p.out = nxt; p.lamfac = Tables<R>::lamfac(c, h);
+    p.in = cur; p.out = nxt; p.lamfac = Tables<R>::lamfac(c, h); p.skip = dyn.skip;
     if ((e = launch_pass<R, TMP, TMP, double2, double2, F_DST | F_LAM>(c, p, s)) != cudaSuccess) return e;
     std::swap(cur, nxt);
   }
   for (int a2 = c->d - 2; a2 >= 1; --a2) {  // middle axes: inverse DST (S is involutory)
     PassParams p = base_params<R>(c, a2, h);
-    p.in = cur; p.out = nxt;
+    p.in = cur; p.out = nxt; p.skip = dyn.skip;
     if ((e = launch_pass<R, TMP, TMP, double2, double2, F_DST>(c, p, s)) != cudaSuccess) return e;
     std::swap(cur, nxt);
   }
@@ -105,12 +132,15 @@ cudaError_t run_precon(rfnse_ctx* c, const TIN* v, const double* in_scale, doubl
     p.in = cur; p.out = z; p.z_add = z_add;
     p.Dr = Tables<R>::Dr(c, D); p.dfac = Tables<R>::dfac(c);
     p.acc_in = w_add; p.acc_out = wtmp; p.ca = a; p.cb = b;
+    with_dyn(p);
     if ((e = launch_pass<R, TMP, TZ, double2, TW, F_DST | F_DSCALE | TX>(c, p, s)) != cudaSuccess) return e;
   }
   if (MATVEC) {
     for (int a2 = 1; a2 < c->d; ++a2) {
       PassParams p = base_params<R>(c, a2, h);
       p.in = z; p.acc_in = wtmp; p.cb = b;
+      with_dyn(p);
+      p.in_dyn_z = (dyn.gs && dyn.zbase) ? 1 : 0;
       if (a2 == c->d - 1) {
         p.acc_out = w;
         e = launch_pass<R, TZ, TZ, TW, double2, F_TOEP_ACC>(c, p, s);
@@ -126,18 +156,18 @@ cudaError_t run_precon(rfnse_ctx* c, const TIN* v, const double* in_scale, doubl
 
 // w = add + a z + b (T - D) z in FP64 (the Toeplitz products by circulant embedding).
 cudaError_t run_matvec_fp64(rfnse_ctx* c, const double2* z, const double* D, double2* w, const double2* add,
-                            double2 a, double2 b, int half) {
+                            double2 a, double2 b, int half, const int* skip) {
   cudaStream_t s = c->stream;
   cudaError_t e;
   const int h = half ? 1 : 0;
   {
     PassParams p = base_params<double>(c, 0, h);
-    p.in = z; p.Dr = D; p.acc_in = add; p.acc_out = w; p.ca = a; p.cb = b;
+    p.in = z; p.Dr = D; p.acc_in = add; p.acc_out = w; p.ca = a; p.cb = b; p.skip = skip;
     if ((e = launch_pass<double, double2, double2, double2, double2, F_TOEP_X>(c, p, s)) != cudaSuccess) return e;
   }
   for (int a2 = 1; a2 < c->d; ++a2) {
     PassParams p = base_params<double>(c, a2, h);
-    p.in = z; p.acc_in = w; p.acc_out = w; p.cb = b;
+    p.in = z; p.acc_in = w; p.acc_out = w; p.cb = b; p.skip = skip;
     if ((e = launch_pass<double, double2, double2, double2, double2, F_TOEP_ACC>(c, p, s)) != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -174,7 +204,7 @@ cudaError_t run_apply_prec(rfnse_ctx* c, const double2* v, double2* z, const dou
 
 cudaError_t run_apply_A(rfnse_ctx* c, const double2* u, double2* out, const double* D, int half) {
   // (D - T + iI) u = i u - (T - D) u
-  return run_matvec_fp64(c, u, D, out, nullptr, kI, kMinusOne, half);
+  return run_matvec_fp64(c, u, D, out, nullptr, kI, kMinusOne, half, nullptr);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -186,6 +216,8 @@ static rfnse_status peek(rfnse_ctx* c, GmresPeek* out) {
   *out = *c->peek;
   return RFNSE_OK;
 }
+
+// ---- host loop -------------------------------------------------------------------------------
 
 // Modified Gram-Schmidt of w against V_0..V_j, then h_{j+1,j}, Givens and the convergence test.
 static void arnoldi_orthogonalise(rfnse_ctx* c, int j) {
@@ -254,7 +286,7 @@ static rfnse_status gmres_fp64(rfnse_ctx* c, const double* D, const double2* f, 
       return RFNSE_ENOCONV;
     }
     // restart: true residual r = f - R x
-    RFNSE_CUDA_TRY(c, run_matvec_fp64(c, x, D, c->r, f, kMinusOne, kMinusI, half));
+    RFNSE_CUDA_TRY(c, run_matvec_fp64(c, x, D, c->r, f, kMinusOne, kMinusI, half, nullptr));
     launch_norm(c->r, c->gs, N, c->red_blocks, c->partials, c->counter, c->stream);
     if ((st = peek(c, &pk))) return st;
     beta = pk.beta;
@@ -322,7 +354,7 @@ static rfnse_status solve_mixed(rfnse_ctx* c, const double* D, const double2* f,
     launch_backsolve(c->gs, k, c->stream);
     launch_combine_f32_add(c->Z32, N, c->gs, k, x, N, c->stream);
     ++outer;
-    RFNSE_CUDA_TRY(c, run_matvec_fp64(c, x, D, c->r, f, kMinusOne, kMinusI, half));
+    RFNSE_CUDA_TRY(c, run_matvec_fp64(c, x, D, c->r, f, kMinusOne, kMinusI, half, nullptr));
     launch_norm(c->r, c->gs, N, c->red_blocks, c->partials, c->counter, c->stream);
     if ((st = peek(c, &pk))) return st;
     beta = pk.beta;
@@ -335,16 +367,184 @@ static rfnse_status solve_mixed(rfnse_ctx* c, const double* D, const double2* f,
   return RFNSE_OK;
 }
 
+// ---- device loop: the solve as one CUDA graph ------------------------------------------------
+
+static SolveCfg make_cfg(const rfnse_ctx* c, int mixed) {
+  SolveCfg cfg{};
+  cfg.m = c->p.restart;
+  cfg.max_it = c->p.max_it;
+  cfg.max_outer = mixed ? (c->p.max_outer > 0 ? c->p.max_outer : 30) : (1 << 30);
+  cfg.mixed = mixed;
+  cfg.tol = c->p.tol;
+  cfg.eta_min = c->p.inner_tol > 0 ? c->p.inner_tol : 1e-6;
+  return cfg;
+}
+
+// Add a conditional WHILE node at the current capture position of stream s and make it the capture's
+// dependency; returns its body graph.
+static cudaError_t add_while_node(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edges = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, &edges, &nd);
+  if (e != cudaSuccess) return e;
+  if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, g, deps, edges, nd, &np)) != cudaSuccess) return e;
+  *body = np.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// One Arnoldi step with operands resolved on the device: z = M^{-1} v_j, w = R z, then MGS/Givens.
+static cudaError_t arnoldi_step_dev(rfnse_ctx* c, int half, const SolveCfg& cfg, cudaGraphConditionalHandle hi,
+                                    int set_cond) {
+  const long long N = c->N;
+  cudaError_t e;
+  Dyn dyn;
+  dyn.gs = c->gs;
+  dyn.vbase = c->V;
+  dyn.ldv = N;
+  if (cfg.mixed) {
+    dyn.zbase = c->Z32;
+    e = run_precon<float, double2, float2, float2, float2, true, true>(
+        c, nullptr, nullptr, nullptr, c->Z32, 0, c->D, c->w, c->wp32, nullptr, kOne, kI, half, c->t1f, c->t2f, dyn);
+  } else {
+    e = run_precon<double, double2, double2, double2, double2, true, true>(
+        c, nullptr, nullptr, nullptr, c->zb, 0, c->D, c->w, c->w, nullptr, kOne, kI, half, c->t1, c->t2, dyn);
+  }
+  if (e != cudaSuccess) return e;
+  return launch_mgs_step(c->gs, c->V, N, c->w, N, c->coop_partials, c->bar, cfg, hi, set_cond, c->coop_blocks,
+                         c->stream);
+}
+
+// Capture the solve of R x = f (c->f, c->x, c->D fixed) for one precision and half flag.
+static cudaError_t build_solve_graph(rfnse_ctx* c, int mixed, int half) {
+  const long long N = c->N;
+  const SolveCfg cfg = make_cfg(c, mixed);
+  cudaStream_t user = c->stream;
+  cudaStream_t s = c->cap_stream;
+  c->stream = s;  // the launch helpers issue on c->stream
+  cudaGraph_t top = nullptr, obody = nullptr, ibody = nullptr;
+  const long long launches_before = g_kernel_launches.load();  // capture records, it does not launch
+  cudaGraphConditionalHandle ho = 0, hi = 0;
+  cudaError_t e = cudaGraphCreate(&top, 0);
+  auto fail = [&](cudaError_t err) {
+    cudaStreamCaptureStatus st;
+    if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(s, &junk);
+    }
+    if (top) cudaGraphDestroy(top);
+    c->stream = user;
+    cudaGetLastError();
+    return err;
+  };
+  if (e != cudaSuccess) return fail(e);
+  if ((e = cudaGraphConditionalHandleCreate(&ho, top, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return fail(e);
+  // solve start: x = 0, beta = ||f||, outer condition
+  if ((e = cudaStreamBeginCaptureToGraph(s, top, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+    return fail(e);
+  launch_zero(c->x, N, s);
+  launch_norm_ctl(c->f, c->gs, N, c->red_blocks, c->partials, c->counter, c->bar, cfg, 0, ho, 1, s);
+  if ((e = add_while_node(s, ho, &obody)) != cudaSuccess) return fail(e);
+  if ((e = cudaStreamEndCapture(s, &top)) != cudaSuccess) return fail(e);
+  // outer body: cycle start, inner loop, solution update, residual and the outer condition
+  if ((e = cudaGraphConditionalHandleCreate(&hi, obody, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+    return fail(e);
+  if ((e = cudaStreamBeginCaptureToGraph(s, obody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
+      cudaSuccess)
+    return fail(e);
+  launch_cycle_begin(c->gs, cfg, hi, ho, 1, s);
+  if ((e = add_while_node(s, hi, &ibody)) != cudaSuccess) return fail(e);
+  launch_backsolve_dev(c->gs, s);
+  if (mixed) {
+    launch_combine_f32_add_dev(c->Z32, N, c->gs, c->x, N, s);
+    if ((e = run_matvec_fp64(c, c->x, c->D, c->r, c->f, kMinusOne, kMinusI, half, nullptr)) != cudaSuccess)
+      return fail(e);
+    launch_norm_ctl(c->r, c->gs, N, c->red_blocks, c->partials, c->counter, c->bar, cfg, 2, ho, 1, s);
+  } else {
+    launch_combine_dev(c->V, N, c->gs, c->r, N, s);
+    if ((e = run_precon<double, double2, double2, double2, double2, false, false>(
+             c, c->r, nullptr, nullptr, c->x, 1, c->D, nullptr, nullptr, nullptr, kOne, kI, half, c->t1, c->t2)) !=
+        cudaSuccess)
+      return fail(e);
+    if ((e = run_matvec_fp64(c, c->x, c->D, c->r, c->f, kMinusOne, kMinusI, half, &c->gs->no_restart)) !=
+        cudaSuccess)
+      return fail(e);
+    launch_norm_ctl(c->r, c->gs, N, c->red_blocks, c->partials, c->counter, c->bar, cfg, 1, ho, 1, s);
+  }
+  if ((e = cudaStreamEndCapture(s, &obody)) != cudaSuccess) return fail(e);
+  // inner body: one Arnoldi step
+  if ((e = cudaStreamBeginCaptureToGraph(s, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
+      cudaSuccess)
+    return fail(e);
+  if ((e = arnoldi_step_dev(c, half, cfg, hi, 1)) != cudaSuccess) return fail(e);
+  if ((e = cudaStreamEndCapture(s, &ibody)) != cudaSuccess) return fail(e);
+  cudaGraphExec_t exec = nullptr;
+  if ((e = cudaGraphInstantiate(&exec, top, 0)) != cudaSuccess) return fail(e);
+  g_kernel_launches.store(launches_before);
+  c->graph[mixed][half] = top;
+  c->graph_exec[mixed][half] = exec;
+  c->stream = user;
+  return cudaSuccess;
+}
+
+// Solve R x = f on the device loop; f, x may be any buffers (copied to / from the graph's own).
+static rfnse_status solve_graph(rfnse_ctx* c, const double* D, const double2* f, double2* x, int half, int* iters,
+                                double* relres, int* outer_out) {
+  const int mixed = c->p.precision == 1 ? 1 : 0;
+  const int h = half ? 1 : 0;
+  const long long N = c->N;
+  if (!c->graph_exec[mixed][h]) RFNSE_CUDA_TRY(c, build_solve_graph(c, mixed, h));
+  if (D != c->D) RFNSE_CUDA_TRY(c, cudaMemcpyAsync(c->D, D, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->stream));
+  if (f != c->f) RFNSE_CUDA_TRY(c, cudaMemcpyAsync(c->f, f, sizeof(double2) * N, cudaMemcpyDeviceToDevice, c->stream));
+  RFNSE_CUDA_TRY(c, prepare_D(c, c->D));
+  RFNSE_CUDA_TRY(c, cudaGraphLaunch(c->graph_exec[mixed][h], c->stream));
+  if (x != c->x) RFNSE_CUDA_TRY(c, cudaMemcpyAsync(x, c->x, sizeof(double2) * N, cudaMemcpyDeviceToDevice, c->stream));
+  GmresPeek pk;
+  rfnse_status st = peek(c, &pk);
+  if (st) return st;
+  *iters = pk.it;
+  *relres = pk.relres;
+  *outer_out = pk.outer;
+  {  // kernels the graph executed: 2 at the start, per Arnoldi step its passes and the MGS kernel,
+     // per cycle the cycle start, back-substitution, update and residual kernels
+    const int d = c->d;
+    const long long step_k = (d == 1 ? 1 : 3 * d - 2) + 1;
+    const long long cycle_k = mixed ? 1 + 1 + 1 + d + 1 : 1 + 1 + 1 + (d == 1 ? 1 : 2 * d - 1) + d + 1;
+    const long long cycles = mixed ? pk.outer : (pk.it > 0 ? pk.outer + 1 : 0);
+    count_launch(2 + step_k * pk.it + cycle_k * cycles);
+  }
+  c->resid_current = mixed && pk.outer > 0;
+  if (pk.err) { c->err = "a bounded device-side wait gave up"; return RFNSE_ETIMEOUT; }
+  if (pk.done == 3) { c->err = "non-finite value in the solve"; return RFNSE_ENUMERIC; }
+  if (pk.beta == 0.0 && pk.it == 0) { *relres = 0.0; return RFNSE_OK; }
+  if (pk.done == 1 || pk.done == 2) return RFNSE_OK;
+  c->err = mixed ? "mixed-precision refinement did not reach tol" : "GMRES reached max_it";
+  return RFNSE_ENOCONV;
+}
+
 rfnse_status solve_block(rfnse_ctx* c, const double* D, const double2* f, double2* x, int half, int* iters,
                          double* relres) {
   int outer = 0;
   rfnse_status st;
-  RFNSE_CUDA_TRY(c, prepare_D(c, D));
-  if (c->p.precision == 1) {
-    st = solve_mixed(c, D, f, x, half, iters, relres, &outer);
+  if (c->use_graphs) {
+    st = solve_graph(c, D, f, x, half, iters, relres, &outer);
   } else {
-    st = gmres_fp64(c, D, f, x, half, iters, relres);
-    outer = 1;
+    RFNSE_CUDA_TRY(c, prepare_D(c, D));
+    if (c->p.precision == 1) {
+      st = solve_mixed(c, D, f, x, half, iters, relres, &outer);
+    } else {
+      st = gmres_fp64(c, D, f, x, half, iters, relres);
+      outer = 1;
+    }
   }
   c->last_outer = outer;
   return st;
@@ -374,13 +574,13 @@ rfnse_status time_step(rfnse_ctx* c, int* iters, double* relres) {
     const double2* u0 = c->u[c->icur];
     const double rdt = c->p.rho * c->p.dt * 0.5;
     launch_diag(u0, nullptr, c->D, rdt, N, c->stream);
-    RFNSE_CUDA_TRY(c, run_matvec_fp64(c, u0, c->D, c->f, nullptr, kOne, kMinusI, 1));
+    RFNSE_CUDA_TRY(c, run_matvec_fp64(c, u0, c->D, c->f, nullptr, kOne, kMinusI, 1, nullptr));
     st = solve_block(c, c->D, c->f, un, 1, &it, relres);
     if (st != RFNSE_OK && st != RFNSE_ENOCONV) return st;
     if (c->p.first_step == 1) {
       int it2 = 0;
       launch_diag(u0, un, c->D, rdt, N, c->stream);
-      RFNSE_CUDA_TRY(c, run_matvec_fp64(c, u0, c->D, c->f, nullptr, kOne, kMinusI, 1));
+      RFNSE_CUDA_TRY(c, run_matvec_fp64(c, u0, c->D, c->f, nullptr, kOne, kMinusI, 1, nullptr));
       st2 = solve_block(c, c->D, c->f, un, 1, &it2, relres);
       if (st2 != RFNSE_OK && st2 != RFNSE_ENOCONV) return st2;
       if (st2 != RFNSE_OK) st = st2;
@@ -394,7 +594,7 @@ rfnse_status time_step(rfnse_ctx* c, int* iters, double* relres) {
     if (c->tu_valid[c->iprev]) {
       launch_rhs_from_tu(up, c->Tu[c->iprev], c->D, c->f, N, c->stream);
     } else {
-      RFNSE_CUDA_TRY(c, run_matvec_fp64(c, up, c->D, c->f, nullptr, kOne, kMinusI, 0));
+      RFNSE_CUDA_TRY(c, run_matvec_fp64(c, up, c->D, c->f, nullptr, kOne, kMinusI, 0, nullptr));
     }
     st = solve_block(c, c->D, c->f, un, 0, &it, relres);
     if (st != RFNSE_OK && st != RFNSE_ENOCONV) return st;

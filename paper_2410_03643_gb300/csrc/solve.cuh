@@ -5,7 +5,7 @@
 namespace rfnse {
 
 cudaError_t run_matvec_fp64(rfnse_ctx* c, const double2* z, const double* D, double2* w, const double2* add,
-                            double2 a, double2 b, int half);
+                            double2 a, double2 b, int half, const int* skip);
 cudaError_t run_dst(rfnse_ctx* c, int axis, const double2* in, double2* out, int precision);
 cudaError_t run_toeplitz(rfnse_ctx* c, int axis, const double2* in, double2* out, int half);
 cudaError_t run_apply_prec(rfnse_ctx* c, const double2* v, double2* z, const double* D, int half, int precision);

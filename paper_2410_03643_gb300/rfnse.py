@@ -46,13 +46,14 @@ class Params(ctypes.Structure):
         ("first_step", ctypes.c_int),
         ("inner_tol", ctypes.c_double),
         ("max_outer", ctypes.c_int),
+        ("device_loop", ctypes.c_int),
     ]
 
 
 EXPORTED = ("rfnse_default_params", "rfnse_create", "rfnse_destroy", "rfnse_last_error", "rfnse_size",
             "rfnse_set_state", "rfnse_get_state", "rfnse_run", "rfnse_apply_A", "rfnse_apply_prec",
             "rfnse_dst", "rfnse_toeplitz", "rfnse_solve", "rfnse_get_coefficients", "rfnse_launch_count",
-            "rfnse_profile", "rfnse_profile_read")
+            "rfnse_profile", "rfnse_profile_read", "rfnse_probe_fma")
 
 K_INSCALE, K_DST, K_LAM, K_DSCALE, K_TOEP_X, K_TOEP_ACC, K_FP32 = 1, 2, 4, 8, 16, 32, 256
 
@@ -103,12 +104,15 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.rfnse_profile.restype = ip
     lib.rfnse_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp, dp, dp]
     lib.rfnse_profile_read.restype = ip
+    lib.rfnse_probe_fma.argtypes = [ip, dp]
+    lib.rfnse_probe_fma.restype = ip
     if path == _build.library_path():
         _lib = lib
     return lib
 
 
-def make_params(problem, precision: int = 0, inner_tol: float = 1e-6, max_outer: int = 30) -> Params:
+def make_params(problem, precision: int = 0, inner_tol: float = 1e-6, max_outer: int = 30,
+                device_loop: int = 1) -> Params:
     """Params from a workloads.Problem."""
     p = Params()
     p.d = problem.d
@@ -127,12 +131,22 @@ def make_params(problem, precision: int = 0, inner_tol: float = 1e-6, max_outer:
     p.first_step = problem.first_step
     p.inner_tol = inner_tol
     p.max_outer = max_outer
+    p.device_loop = device_loop
     return p
 
 
 def launch_count() -> int:
     """Kernels launched by librfnse.so in this process."""
     return int(load_library().rfnse_launch_count())
+
+
+def probe_fma(fp64: bool) -> float:
+    """Measured FMA throughput of the current device in flop/s (FP64 or FP32)."""
+    v = ctypes.c_double()
+    st = load_library().rfnse_probe_fma(int(fp64), ctypes.byref(v))
+    if st != RFNSE_OK:
+        raise RfnseError(st, "rfnse_probe_fma failed")
+    return v.value
 
 
 def _ptr(t) -> int:
@@ -142,13 +156,14 @@ def _ptr(t) -> int:
 class Solver:
     """One solver context (rfnse_create).  `stream` is a torch.cuda.Stream or None (current)."""
 
-    def __init__(self, problem, precision: int = 0, stream=None, inner_tol: float = 1e-6, max_outer: int = 30):
+    def __init__(self, problem, precision: int = 0, stream=None, inner_tol: float = 1e-6, max_outer: int = 30,
+                 device_loop: int = 1):
         import torch
         self.lib = load_library()
         self.problem = problem
         self.precision = precision
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        self.params = make_params(problem, precision, inner_tol, max_outer)
+        self.params = make_params(problem, precision, inner_tol, max_outer, device_loop)
         h = ctypes.c_void_p()
         st = self.lib.rfnse_create(ctypes.byref(self.params), ctypes.c_void_p(self.stream.cuda_stream),
                                    ctypes.byref(h))

@@ -166,6 +166,27 @@ def test_trajectory_matches_oracle(p, precision):
             assert abs(int(iters[k]) - its_ref[k]) <= 1, (k, iters, its_ref)
 
 
+@pytest.mark.parametrize("p", SMALL, ids=IDS)
+@pytest.mark.parametrize("precision", (0, 1))
+def test_host_and_device_loops_agree(p, precision):
+    """The solve driven by the host after every Arnoldi step and the solve as one CUDA graph with
+    device-decided loops give the same trajectory (reduction orders differ: rounding level) and the
+    same iteration counts within 1."""
+    p = p.replace(tol=1e-10)
+    u0 = W.u0_sech_product(p, [1.0] * p.d) if p.d > 1 else W.u0_sech_1d(p)
+    out = []
+    for loop in (0, 1):
+        s = Solver(p, precision=precision, device_loop=loop)
+        s.set_state(dev(u0))
+        traj = torch.empty(4 * p.size, dtype=torch.complex128, device="cuda")
+        iters, _ = s.run(4, traj)
+        out.append((traj.cpu().numpy().reshape((4,) + p.shape), iters))
+        s.close()
+    for k in range(4):
+        assert rel(out[1][0][k], out[0][0][k]) < (1e-11 if precision == 0 else 1e-9)
+        assert abs(int(out[1][1][k]) - int(out[0][1][k])) <= 1
+
+
 def test_first_step_predictor_only_matches_oracle():
     p = SMALL[2].replace(first_step=0, tol=1e-10)
     u0 = W.u0_sech_product(p, [1.0, 1.0])

@@ -55,6 +55,7 @@ def test_params_struct_matches_defaults(libpath):
     lib.rfnse_default_params(ctypes.byref(p))
     assert p.d == 1 and p.restart == 20 and p.max_it == 2000 and p.omega == 1.0
     assert p.tol == 1e-10 and p.first_step == 1 and p.inner_tol == 1e-6 and p.max_outer == 30
+    assert p.device_loop == 1
 
 
 def test_create_rejects_invalid_params_without_gpu_work(libpath):
