@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d", choices=["2d", "3d", "1d"])
+    ap.add_argument("--workload", default="2d", choices=["2d", "3d", "1d", "batched"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
@@ -67,6 +67,11 @@ def workload(name):
         inst = [(p, u0)]
         desc = {"workload": "3d_n255^3_alpha1.7_rho1_dt0.01_tol1e-8", "d": 3, "n": [255, 255, 255],
                 "box": [-8, 8], "alphas": [1.7], "instances": 1}
+    elif name == "batched":
+        inst, _ = W.config_batched()
+        desc = {"workload": "batched_64x2d_n{127,255,511}^2_seed2410_dt0.005_tol1e-10", "d": 2,
+                "instances": len(inst), "dof_per_step": int(sum(p.size for p, _ in inst)),
+                "sampling": "n_x, n_y iid from {127,255,511}; alpha~U[1.1,1.95]; rho~U[0.5,3]; k~U[-3,3]"}
     else:
         p, u0, _ = W.config_1d()
         inst = [(p, u0)]
@@ -433,6 +438,79 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """The 64-instance batch: one bench step = one time step of every instance (one graph launch)."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2410_03643_gb300 import build, rfnse
+    build.build_library()
+    inst, desc = workload("batched")
+    main = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    dof = sum(p.size for p, _ in inst)
+
+    def timed(precision, clocks=None):
+        b = rfnse.Batch([p for p, _ in inst], precision=precision, stream=main)
+        for i, (p, u0) in enumerate(inst):
+            b.set_state(i, torch.from_numpy(u0.ravel().copy()).to(dev))
+        b.run(max(args.warmup, 3))                  # the first steps run instance by instance
+        torch.cuda.synchronize()
+        l0 = rfnse.launch_count()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        its = []
+        barrier(world)
+        if clocks:
+            clocks.mark_on()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            evs[k][0].record(main)
+            it, _ = b.run(1)
+            evs[k][1].record(main)
+            its.append(it)
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.mark_off()
+        ms = sum(a.elapsed_time(e) for a, e in evs)
+        launches = rfnse.launch_count() - l0
+        states = [b.get_state(i)[1] for i in range(b.count)]
+        b.close()
+        return ms, launches, np.array(its), states
+
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    ms, launches, its, st_mixed = timed(1, clocks)
+    clk = clocks.stop() if clocks else None
+    ms = reduce_max(ms, world, dev)
+    out = {"metric": METRIC, "value": world * dof * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
+           "data": "synthetic (closed-form initial data of the paper's shape, seeded parameters)",
+           "config": dict(desc, precision="mixed", l2="256 MiB buffer written between timed steps",
+                          parallelism=f"{world} GPU(s); one CUDA graph launch per batch step"),
+           "gpu_launches": launches, "iters_per_solve_mean": float(its.mean())}
+    if clk:
+        out["clocks"] = clk
+    if not args.no_fp64:
+        ms64, _, its64, st64 = timed(0)
+        ms64 = reduce_max(ms64, world, dev)
+        errs = [float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)) for a, b in zip(st_mixed, st64)]
+        out["fp64"] = {"value": world * dof * args.steps / (ms64 * 1e-3), "ms_per_step": ms64 / args.steps,
+                       "iters_per_solve_mean": float(its64.mean())}
+        out["mixed_vs_fp64_rel_l2_after_run"] = max(errs)
+        out["mixed_speedup_vs_fp64"] = ms64 / ms
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def alu_probe():
     import torch
     from paper_2410_03643_gb300 import build, rfnse
@@ -451,6 +529,8 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -109,6 +109,35 @@ int rfnse_get_state(rfnse_ctx* ctx, void* u_prev, void* u_cur, int* step, int on
    Errors: EINVAL, ECUDA, ENOCONV (the step is still taken), ENUMERIC. */
 int rfnse_run(rfnse_ctx* ctx, int nsteps, void* traj, int* iters, double* relres, int on_device);
 
+/* ---- batches of independent instances ----------------------------------------------------------- */
+
+typedef struct rfnse_batch rfnse_batch;
+
+/* Create `count` independent instances (params[i]: own grid, alpha, rho, dt, tolerance, precision),
+   each a context with its own CUDA stream owned by the batch.  stream: the caller's cudaStream_t on
+   which the batch step runs (may be NULL).  Errors: EINVAL, ENOMEM, ECUDA; on failure *out is NULL
+   and rfnse_batch_last_error(NULL) describes the failure. */
+int rfnse_batch_create(const rfnse_params* params, int count, void* stream, rfnse_batch** out);
+
+/* Release the batch and its instances (NULL is accepted). */
+void rfnse_batch_destroy(rfnse_batch* b);
+
+/* Text of the last error of b (b = NULL: of the last failed rfnse_batch_create). */
+const char* rfnse_batch_last_error(const rfnse_batch* b);
+
+/* The context of instance i (owned by the batch: do not destroy it).  Use rfnse_set_state,
+   rfnse_get_state and rfnse_get_coefficients on it to load and read each instance. */
+rfnse_ctx* rfnse_batch_context(rfnse_batch* b, int i);
+
+/* Advance every instance by nsteps time steps of the scheme (as rfnse_run).  While any instance is at
+   its first step (or has a fresh state), the instances step one after another on their streams; once
+   all are past it, one time step of the whole batch is a single CUDA graph launch: per instance its
+   right-hand side, its solve with device-decided loops, the update of the mixed form's cached T u
+   and the rotation of its history, then a gather of every instance's statistics.  iters, relres
+   (host, may be NULL): nsteps * count values, step-major ([s * count + i]).  Errors: EINVAL, ECUDA,
+   ENOCONV (every step is still taken), ENUMERIC, ETIMEOUT. */
+int rfnse_batch_run(rfnse_batch* b, int nsteps, int* iters, double* relres);
+
 /* ---- building blocks (device pointers; used by the parity tests) ---------------------------- */
 
 /* out = (D - T + iI) u, the system matrix of eq. 'equ3' (Sec. 2).  half = 1 uses mu_a/2 (first

@@ -71,6 +71,7 @@ void free_ctx(rfnse_ctx* c) {
       if (c->graph[a][h]) cudaGraphDestroy(c->graph[a][h]);
     }
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->cap_stream2) cudaStreamDestroy(c->cap_stream2);
   cudaFree(c->bar);
   cudaFree(c->coop_partials);
   delete c;
@@ -202,6 +203,7 @@ int rfnse_create(const rfnse_params* p, void* stream, rfnse_ctx** out) {
   chk(dalloc(&c->bar, 1));
   chk(dalloc(&c->coop_partials, 2 * (size_t)c->coop_blocks));
   if (e == cudaSuccess) chk(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  if (e == cudaSuccess) chk(cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking));
   chk(dalloc(&c->partials, 1024));
   chk(dalloc(&c->counter, 1));
   chk(dalloc(&c->gs, 1));

@@ -1,0 +1,291 @@
+// Batched time stepping of many independent instances (different grids, alpha, rho, dt): every
+// instance keeps its own context and stream; once all instances are past their first step, one time
+// step of the whole batch is a single CUDA graph launch.  The graph holds, for every instance in its
+// own branch, the right-hand side, the solve with its device-decided loops (capture_solve), the update
+// of the cached T u (mixed form) and the rotation of the history by copies; it ends by gathering every
+// instance's statistics into pinned host memory.
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+#include "internal.cuh"
+#include "solve.cuh"
+
+using namespace rfnse;
+
+struct rfnse_batch {
+  int count = 0;
+  std::vector<rfnse_ctx*> ctx;
+  std::vector<cudaStream_t> streams;  // one per instance (owned)
+  cudaStream_t stream = nullptr;      // the caller's stream: the batch graph runs on it
+  cudaStream_t cap = nullptr;         // private stream that captures the batch graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  GmresState** d_gs = nullptr;        // device array of the instances' GMRES states
+  GmresPeek* d_peeks = nullptr;
+  GmresPeek* h_peeks = nullptr;       // pinned
+  std::vector<cudaEvent_t> events;
+  std::string err;
+};
+
+namespace {
+
+const double2 kOne = {1.0, 0.0};
+const double2 kMinusI = {0.0, -1.0};
+
+void free_batch(rfnse_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (rfnse_ctx* c : b->ctx) rfnse_destroy(c);
+  for (cudaStream_t s : b->streams)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  cudaFree(b->d_gs);
+  cudaFree(b->d_peeks);
+  if (b->h_peeks) cudaFreeHost(b->h_peeks);
+  delete b;
+}
+
+// Put the history in the canonical slots (u_prev in u[0], u_cur in u[1], each with its cached T u) so a
+// captured step can use fixed pointers.  Every copy goes into the slot that is free at that moment.
+cudaError_t normalise_history(rfnse_ctx* c) {
+  int p = c->iprev, q = c->icur, sp = 3 - p - q;
+  if (p == 0 && q == 1) return cudaSuccess;
+  const size_t bytes = sizeof(double2) * (size_t)c->N;
+  cudaError_t e = cudaSuccess;
+  auto move = [&](int from, int to) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->u[to], c->u[from], bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && c->Tu[to])
+      e = cudaMemcpyAsync(c->Tu[to], c->Tu[from], bytes, cudaMemcpyDeviceToDevice, c->stream);
+    c->tu_valid[to] = c->tu_valid[from];
+  };
+  if (q == 0) {  // u_cur sits in slot 0: move it to the free slot first
+    move(0, sp);
+    q = sp;
+    sp = 0;
+  }
+  if (p != 0) {  // slot 0 is free now
+    move(p, 0);
+    sp = p;
+    p = 0;
+  }
+  if (q != 1) move(q, 1);  // slot 1 is free now
+  c->iprev = 0;
+  c->icur = 1;
+  c->tu_valid[2] = false;
+  return e;
+}
+
+// Record one steady-state time step of instance c (history in the canonical slots) on its stream,
+// which is capturing into graph g.
+cudaError_t capture_step(rfnse_ctx* c, cudaGraph_t g) {
+  const long long N = c->N;
+  const size_t bytes = sizeof(double2) * (size_t)N;
+  cudaStream_t s = c->stream;
+  const int mixed = c->p.precision == 1;
+  cudaError_t e;
+  launch_diag(c->u[1], nullptr, c->D, c->p.rho * c->p.dt, N, s);
+  if (mixed) {
+    launch_rhs_from_tu(c->u[0], c->Tu[0], c->D, c->f, N, s);
+  } else if ((e = run_matvec_fp64(c, c->u[0], c->D, c->f, nullptr, kOne, kMinusI, 0, nullptr)) != cudaSuccess) {
+    return e;
+  }
+  if ((e = prepare_D(c, c->D)) != cudaSuccess) return e;
+  if ((e = capture_solve(c, mixed, 0, g, s)) != cudaSuccess) return e;
+  if (mixed) launch_tu_from_residual_dev(c->gs, c->D, c->f, c->x, c->r, c->Tu[2], N, s);
+  if ((e = cudaMemcpyAsync(c->u[0], c->u[1], bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(c->u[1], c->x, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+  if (mixed) {
+    if ((e = cudaMemcpyAsync(c->Tu[0], c->Tu[1], bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(c->Tu[1], c->Tu[2], bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t build_batch_graph(rfnse_batch* b) {
+  const long long launches_before = g_kernel_launches.load();
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(b->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    cudaEvent_t fork = b->events[0];
+    e = cudaEventRecord(fork, b->cap);
+    for (int i = 0; i < b->count && e == cudaSuccess; ++i) {
+      rfnse_ctx* c = b->ctx[i];
+      e = cudaStreamWaitEvent(c->stream, fork, 0);
+      if (e == cudaSuccess) e = capture_step(c, g);
+      if (e == cudaSuccess) e = cudaEventRecord(b->events[1 + i], c->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->events[1 + i], 0);
+    }
+    if (e == cudaSuccess) {
+      launch_gather_peeks(b->d_gs, b->d_peeks, b->count, b->cap);
+      e = cudaMemcpyAsync(b->h_peeks, b->d_peeks, sizeof(GmresPeek) * b->count, cudaMemcpyDeviceToHost, b->cap);
+    }
+    cudaGraph_t out = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(b->cap, &out);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+  g_kernel_launches.store(launches_before);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    b->exec = nullptr;
+    cudaGetLastError();
+    return e;
+  }
+  b->graph = g;
+  return cudaSuccess;
+}
+
+bool steady(const rfnse_ctx* c) { return c->step >= 1 && (c->p.precision == 0 || c->tu_valid[c->iprev]); }
+
+// Kernels one captured solve executed, from its statistics (as counted for stand-alone solves).
+long long solve_kernels(const rfnse_ctx* c, const GmresPeek& pk) {
+  const int d = c->d;
+  const int mixed = c->p.precision == 1;
+  const long long step_k = (d == 1 ? 1 : 3 * d - 2) + 1;
+  const long long cycle_k = mixed ? 1 + 1 + 1 + d + 1 : 1 + 1 + 1 + (d == 1 ? 1 : 2 * d - 1) + d + 1;
+  const long long cycles = mixed ? pk.outer : (pk.it > 0 ? pk.outer + 1 : 0);
+  return 2 + step_k * pk.it + cycle_k * cycles;
+}
+
+thread_local std::string g_batch_create_error;
+
+}  // namespace
+
+extern "C" {
+
+int rfnse_batch_create(const rfnse_params* params, int count, void* stream, rfnse_batch** out) {
+  if (!out) return RFNSE_EINVAL;
+  *out = nullptr;
+  if (!params || count < 1) {
+    g_batch_create_error = "need count >= 1 parameter sets";
+    return RFNSE_EINVAL;
+  }
+  rfnse_batch* b = new (std::nothrow) rfnse_batch();
+  if (!b) return RFNSE_ENOMEM;
+  b->count = count;
+  b->stream = (cudaStream_t)stream;
+  b->ctx.assign(count, nullptr);
+  b->streams.assign(count, nullptr);
+  int st = RFNSE_OK;
+  for (int i = 0; i < count && st == RFNSE_OK; ++i) {
+    if (cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) != cudaSuccess) {
+      st = RFNSE_ECUDA;
+      break;
+    }
+    st = rfnse_create(&params[i], b->streams[i], &b->ctx[i]);
+    if (st != RFNSE_OK) g_batch_create_error = "instance " + std::to_string(i) + ": " + rfnse_last_error(nullptr);
+    if (st == RFNSE_OK && !b->ctx[i]->Tu[0] && params[i].precision == 1) st = RFNSE_ENOMEM;
+  }
+  if (st == RFNSE_OK) {
+    b->events.assign(count + 1, nullptr);
+    for (auto& e : b->events)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) st = RFNSE_ECUDA;
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) st = RFNSE_ECUDA;
+    if (cudaMalloc((void**)&b->d_gs, sizeof(GmresState*) * count) != cudaSuccess ||
+        cudaMalloc((void**)&b->d_peeks, sizeof(GmresPeek) * count) != cudaSuccess ||
+        cudaMallocHost((void**)&b->h_peeks, sizeof(GmresPeek) * count) != cudaSuccess)
+      st = RFNSE_ENOMEM;
+  }
+  if (st == RFNSE_OK) {
+    std::vector<GmresState*> h(count);
+    for (int i = 0; i < count; ++i) h[i] = b->ctx[i]->gs;
+    if (cudaMemcpy(b->d_gs, h.data(), sizeof(GmresState*) * count, cudaMemcpyHostToDevice) != cudaSuccess)
+      st = RFNSE_ECUDA;
+  }
+  if (st != RFNSE_OK) {
+    if (g_batch_create_error.empty()) g_batch_create_error = "batch set-up failed";
+    free_batch(b);
+    return st;
+  }
+  *out = b;
+  return RFNSE_OK;
+}
+
+void rfnse_batch_destroy(rfnse_batch* b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  free_batch(b);
+}
+
+const char* rfnse_batch_last_error(const rfnse_batch* b) { return b ? b->err.c_str() : g_batch_create_error.c_str(); }
+
+rfnse_ctx* rfnse_batch_context(rfnse_batch* b, int i) {
+  if (!b || i < 0 || i >= b->count) return nullptr;
+  return b->ctx[i];
+}
+
+int rfnse_batch_run(rfnse_batch* b, int nsteps, int* iters, double* relres) {
+  if (!b || nsteps < 0) return RFNSE_EINVAL;
+  int worst = RFNSE_OK;
+  for (int s = 0; s < nsteps; ++s) {
+    bool all_steady = true;
+    for (rfnse_ctx* c : b->ctx) all_steady = all_steady && steady(c);
+    if (!all_steady) {  // first steps: every instance on its own (host-driven) until all are steady
+      for (int i = 0; i < b->count; ++i) {
+        int it = 0;
+        double rr = 0.0;
+        const int st = rfnse_run(b->ctx[i], 1, nullptr, &it, &rr, 1);
+        if (st != RFNSE_OK && st != RFNSE_ENOCONV) {
+          b->err = "instance " + std::to_string(i) + ": " + rfnse_last_error(b->ctx[i]);
+          return st;
+        }
+        if (st == RFNSE_ENOCONV) worst = RFNSE_ENOCONV;
+        if (iters) iters[(size_t)s * b->count + i] = it;
+        if (relres) relres[(size_t)s * b->count + i] = rr;
+      }
+      continue;
+    }
+    for (rfnse_ctx* c : b->ctx) {
+      if (normalise_history(c) != cudaSuccess) {
+        b->err = "history normalisation failed";
+        return RFNSE_ECUDA;
+      }
+    }
+    for (rfnse_ctx* c : b->ctx) {
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        b->err = "stream synchronisation failed";
+        return RFNSE_ECUDA;
+      }
+    }
+    if (!b->exec) {
+      const cudaError_t e = build_batch_graph(b);
+      if (e != cudaSuccess) {
+        b->err = std::string("batch graph: ") + cudaGetErrorString(e);
+        return RFNSE_ECUDA;
+      }
+    }
+    cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+      b->err = std::string("batch step: ") + cudaGetErrorString(e);
+      return RFNSE_ECUDA;
+    }
+    for (int i = 0; i < b->count; ++i) {
+      rfnse_ctx* c = b->ctx[i];
+      const GmresPeek& pk = b->h_peeks[i];
+      count_launch(solve_kernels(c, pk) + 2 + (c->p.precision == 1 ? 2 : c->d) + 1);
+      c->step += 1;
+      c->tu_valid[0] = c->tu_valid[1] = (c->p.precision == 1);
+      c->tu_valid[2] = false;
+      if (iters) iters[(size_t)s * b->count + i] = pk.it;
+      if (relres) relres[(size_t)s * b->count + i] = pk.relres;
+      if (pk.err) {
+        b->err = "instance " + std::to_string(i) + ": a bounded device-side wait gave up";
+        return RFNSE_ETIMEOUT;
+      }
+      if (pk.done == 3) {
+        b->err = "instance " + std::to_string(i) + ": non-finite value in the solve";
+        return RFNSE_ENUMERIC;
+      }
+      const bool trivial = pk.beta == 0.0 && pk.it == 0;
+      if (!trivial && pk.done != 1 && pk.done != 2) worst = RFNSE_ENOCONV;
+    }
+  }
+  return worst;
+}
+
+}  // extern "C"

@@ -284,6 +284,34 @@ __global__ void k_combine_f32_add_dev(const float2* __restrict__ Z, long long ld
   }
 }
 
+// Mixed form, inside a captured time step: T x from the solve's final residual r = f - x - i(T - D)x,
+// Tx = D x - i (f - x - r); when the solve did no refinement cycle (f = 0, x = 0) Tx = 0.
+__global__ void k_tu_from_residual_dev(const GmresState* gs, const double* __restrict__ D,
+                                       const double2* __restrict__ f, const double2* __restrict__ x,
+                                       const double2* __restrict__ r, double2* __restrict__ Tu, long long N) {
+  const bool have = gs->outer > 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    if (!have) {
+      Tu[i] = make_double2(0.0, 0.0);
+      continue;
+    }
+    const double2 fv = f[i], xv = x[i], rv = r[i];
+    const double d = D[i];
+    const double qx = fv.x - xv.x - rv.x, qy = fv.y - xv.y - rv.y;
+    Tu[i] = make_double2(d * xv.x + qy, d * xv.y - qx);
+  }
+}
+
+// Copy the host-read prefix of every instance's GMRES state into one array.
+__global__ void k_gather_peeks(GmresState* const* gs, GmresPeek* out, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = *reinterpret_cast<const GmresPeek*>(gs[i]);
+}
+
+void launch_tu_from_residual_dev(const GmresState* gs, const double* D, const double2* f, const double2* x,
+                                 const double2* r, double2* Tu, long long N, cudaStream_t s);
+void launch_gather_peeks(GmresState* const* gs, GmresPeek* out, int count, cudaStream_t s);
+
 static inline unsigned ew_blocks_c(long long N) {
   long long b = (N + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
@@ -329,6 +357,15 @@ void launch_cycle_begin(GmresState* gs, const SolveCfg& cfg, cudaGraphConditiona
                         cudaGraphConditionalHandle h_outer, int set_cond, cudaStream_t s) {
   count_launch();
   k_cycle_begin<<<1, 1, 0, s>>>(gs, cfg, h_inner, h_outer, set_cond);
+}
+void launch_tu_from_residual_dev(const GmresState* gs, const double* D, const double2* f, const double2* x,
+                                 const double2* r, double2* Tu, long long N, cudaStream_t s) {
+  count_launch();
+  k_tu_from_residual_dev<<<ew_blocks_c(N), 256, 0, s>>>(gs, D, f, x, r, Tu, N);
+}
+void launch_gather_peeks(GmresState* const* gs, GmresPeek* out, int count, cudaStream_t s) {
+  count_launch();
+  k_gather_peeks<<<(count + 127) / 128, 128, 0, s>>>(gs, out, count);
 }
 void launch_backsolve_dev(GmresState* gs, cudaStream_t s) {
   count_launch();

@@ -76,6 +76,9 @@ void launch_norm_ctl(const double2* x, GmresState* gs, long long N, int blocks, 
 void launch_cycle_begin(GmresState* gs, const SolveCfg& cfg, cudaGraphConditionalHandle h_inner,
                         cudaGraphConditionalHandle h_outer, int set_cond, cudaStream_t s);
 void launch_backsolve_dev(GmresState* gs, cudaStream_t s);
+void launch_tu_from_residual_dev(const GmresState* gs, const double* D, const double2* f, const double2* x,
+                                 const double2* r, double2* Tu, long long N, cudaStream_t s);
+void launch_gather_peeks(GmresState* const* gs, GmresPeek* out, int count, cudaStream_t s);
 void launch_combine_dev(const double2* V, long long ldv, const GmresState* gs, double2* out, long long N,
                         cudaStream_t s);
 void launch_combine_f32_add_dev(const float2* Z, long long ldz, const GmresState* gs, double2* x, long long N,
@@ -178,7 +181,8 @@ struct rfnse_ctx {
   double* coop_partials = nullptr;   // 2 * coop_blocks
   int coop_blocks = 1;
   bool use_graphs = true;
-  cudaStream_t cap_stream = nullptr;  // private stream used only to capture the graphs
+  cudaStream_t cap_stream = nullptr;   // private stream that captures the loop bodies
+  cudaStream_t cap_stream2 = nullptr;  // private stream that captures a stand-alone solve graph
   cudaGraph_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   cudaGraphExec_t graph_exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   // per-step statistics of the last solve

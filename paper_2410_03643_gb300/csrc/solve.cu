@@ -424,53 +424,49 @@ static cudaError_t arnoldi_step_dev(rfnse_ctx* c, int half, const SolveCfg& cfg,
                          c->stream);
 }
 
-// Capture the solve of R x = f (c->f, c->x, c->D fixed) for one precision and half flag.
-static cudaError_t build_solve_graph(rfnse_ctx* c, int mixed, int half) {
+// Record the solve of R x = f (c->f, c->x, c->D fixed) for one precision and half flag at the current
+// capture position of stream s, which is capturing into graph g: x = 0, ||f||, then the outer WHILE
+// node.  The loop bodies are captured on the context's private body stream.
+cudaError_t capture_solve(rfnse_ctx* c, int mixed, int half, cudaGraph_t g, cudaStream_t s) {
   const long long N = c->N;
   const SolveCfg cfg = make_cfg(c, mixed);
   cudaStream_t user = c->stream;
-  cudaStream_t s = c->cap_stream;
-  c->stream = s;  // the launch helpers issue on c->stream
-  cudaGraph_t top = nullptr, obody = nullptr, ibody = nullptr;
-  const long long launches_before = g_kernel_launches.load();  // capture records, it does not launch
+  cudaStream_t bs = c->cap_stream;
+  cudaGraph_t obody = nullptr, ibody = nullptr;
   cudaGraphConditionalHandle ho = 0, hi = 0;
-  cudaError_t e = cudaGraphCreate(&top, 0);
+  cudaError_t e;
   auto fail = [&](cudaError_t err) {
     cudaStreamCaptureStatus st;
-    if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+    if (cudaStreamIsCapturing(bs, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
       cudaGraph_t junk = nullptr;
-      cudaStreamEndCapture(s, &junk);
+      cudaStreamEndCapture(bs, &junk);
     }
-    if (top) cudaGraphDestroy(top);
     c->stream = user;
-    cudaGetLastError();
     return err;
   };
-  if (e != cudaSuccess) return fail(e);
-  if ((e = cudaGraphConditionalHandleCreate(&ho, top, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return fail(e);
+  if ((e = cudaGraphConditionalHandleCreate(&ho, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return fail(e);
   // solve start: x = 0, beta = ||f||, outer condition
-  if ((e = cudaStreamBeginCaptureToGraph(s, top, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
-    return fail(e);
+  c->stream = s;
   launch_zero(c->x, N, s);
   launch_norm_ctl(c->f, c->gs, N, c->red_blocks, c->partials, c->counter, c->bar, cfg, 0, ho, 1, s);
   if ((e = add_while_node(s, ho, &obody)) != cudaSuccess) return fail(e);
-  if ((e = cudaStreamEndCapture(s, &top)) != cudaSuccess) return fail(e);
   // outer body: cycle start, inner loop, solution update, residual and the outer condition
+  c->stream = bs;
   if ((e = cudaGraphConditionalHandleCreate(&hi, obody, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
     return fail(e);
-  if ((e = cudaStreamBeginCaptureToGraph(s, obody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
+  if ((e = cudaStreamBeginCaptureToGraph(bs, obody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
       cudaSuccess)
     return fail(e);
-  launch_cycle_begin(c->gs, cfg, hi, ho, 1, s);
-  if ((e = add_while_node(s, hi, &ibody)) != cudaSuccess) return fail(e);
-  launch_backsolve_dev(c->gs, s);
+  launch_cycle_begin(c->gs, cfg, hi, ho, 1, bs);
+  if ((e = add_while_node(bs, hi, &ibody)) != cudaSuccess) return fail(e);
+  launch_backsolve_dev(c->gs, bs);
   if (mixed) {
-    launch_combine_f32_add_dev(c->Z32, N, c->gs, c->x, N, s);
+    launch_combine_f32_add_dev(c->Z32, N, c->gs, c->x, N, bs);
     if ((e = run_matvec_fp64(c, c->x, c->D, c->r, c->f, kMinusOne, kMinusI, half, nullptr)) != cudaSuccess)
       return fail(e);
-    launch_norm_ctl(c->r, c->gs, N, c->red_blocks, c->partials, c->counter, c->bar, cfg, 2, ho, 1, s);
+    launch_norm_ctl(c->r, c->gs, N, c->red_blocks, c->partials, c->counter, c->bar, cfg, 2, ho, 1, bs);
   } else {
-    launch_combine_dev(c->V, N, c->gs, c->r, N, s);
+    launch_combine_dev(c->V, N, c->gs, c->r, N, bs);
     if ((e = run_precon<double, double2, double2, double2, double2, false, false>(
              c, c->r, nullptr, nullptr, c->x, 1, c->D, nullptr, nullptr, nullptr, kOne, kI, half, c->t1, c->t2)) !=
         cudaSuccess)
@@ -478,21 +474,42 @@ static cudaError_t build_solve_graph(rfnse_ctx* c, int mixed, int half) {
     if ((e = run_matvec_fp64(c, c->x, c->D, c->r, c->f, kMinusOne, kMinusI, half, &c->gs->no_restart)) !=
         cudaSuccess)
       return fail(e);
-    launch_norm_ctl(c->r, c->gs, N, c->red_blocks, c->partials, c->counter, c->bar, cfg, 1, ho, 1, s);
+    launch_norm_ctl(c->r, c->gs, N, c->red_blocks, c->partials, c->counter, c->bar, cfg, 1, ho, 1, bs);
   }
-  if ((e = cudaStreamEndCapture(s, &obody)) != cudaSuccess) return fail(e);
+  if ((e = cudaStreamEndCapture(bs, &obody)) != cudaSuccess) return fail(e);
   // inner body: one Arnoldi step
-  if ((e = cudaStreamBeginCaptureToGraph(s, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
+  if ((e = cudaStreamBeginCaptureToGraph(bs, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
       cudaSuccess)
     return fail(e);
   if ((e = arnoldi_step_dev(c, half, cfg, hi, 1)) != cudaSuccess) return fail(e);
-  if ((e = cudaStreamEndCapture(s, &ibody)) != cudaSuccess) return fail(e);
+  if ((e = cudaStreamEndCapture(bs, &ibody)) != cudaSuccess) return fail(e);
+  c->stream = user;
+  return cudaSuccess;
+}
+
+// The solve alone as an instantiated graph, cached per (precision, half).
+static cudaError_t build_solve_graph(rfnse_ctx* c, int mixed, int half) {
+  cudaStream_t s = c->cap_stream2;
+  cudaGraph_t top = nullptr;
+  const long long launches_before = g_kernel_launches.load();  // capture records, it does not launch
+  cudaError_t e = cudaGraphCreate(&top, 0);
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s, top, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    e = capture_solve(c, mixed, half, top, s);
+    cudaGraph_t out = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(s, &out);
+    if (e == cudaSuccess) e = e2;
+  }
   cudaGraphExec_t exec = nullptr;
-  if ((e = cudaGraphInstantiate(&exec, top, 0)) != cudaSuccess) return fail(e);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, top, 0);
   g_kernel_launches.store(launches_before);
+  if (e != cudaSuccess) {
+    if (top) cudaGraphDestroy(top);
+    cudaGetLastError();
+    return e;
+  }
   c->graph[mixed][half] = top;
   c->graph_exec[mixed][half] = exec;
-  c->stream = user;
   return cudaSuccess;
 }
 

@@ -53,7 +53,8 @@ class Params(ctypes.Structure):
 EXPORTED = ("rfnse_default_params", "rfnse_create", "rfnse_destroy", "rfnse_last_error", "rfnse_size",
             "rfnse_set_state", "rfnse_get_state", "rfnse_run", "rfnse_apply_A", "rfnse_apply_prec",
             "rfnse_dst", "rfnse_toeplitz", "rfnse_solve", "rfnse_get_coefficients", "rfnse_launch_count",
-            "rfnse_profile", "rfnse_profile_read", "rfnse_probe_fma")
+            "rfnse_profile", "rfnse_profile_read", "rfnse_probe_fma", "rfnse_batch_create",
+            "rfnse_batch_destroy", "rfnse_batch_last_error", "rfnse_batch_context", "rfnse_batch_run")
 
 K_INSCALE, K_DST, K_LAM, K_DSCALE, K_TOEP_X, K_TOEP_ACC, K_FP32 = 1, 2, 4, 8, 16, 32, 256
 
@@ -106,6 +107,16 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.rfnse_profile_read.restype = ip
     lib.rfnse_probe_fma.argtypes = [ip, dp]
     lib.rfnse_probe_fma.restype = ip
+    lib.rfnse_batch_create.argtypes = [ctypes.POINTER(Params), ip, vp, ctypes.POINTER(vp)]
+    lib.rfnse_batch_create.restype = ip
+    lib.rfnse_batch_destroy.argtypes = [vp]
+    lib.rfnse_batch_destroy.restype = None
+    lib.rfnse_batch_last_error.argtypes = [vp]
+    lib.rfnse_batch_last_error.restype = cp
+    lib.rfnse_batch_context.argtypes = [vp, ip]
+    lib.rfnse_batch_context.restype = vp
+    lib.rfnse_batch_run.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), dp]
+    lib.rfnse_batch_run.restype = ip
     if path == _build.library_path():
         _lib = lib
     return lib
@@ -287,3 +298,66 @@ class Solver:
         self._check(self.lib.rfnse_get_coefficients(self.h, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                                     lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return c, lam
+
+
+class Batch:
+    """A batch of independent instances (rfnse_batch_create): one graph launch per time step of all."""
+
+    def __init__(self, problems, precision: int = 0, stream=None, inner_tol: float = 1e-6, max_outer: int = 30,
+                 device_loop: int = 1):
+        import torch
+        self.lib = load_library()
+        self.problems = list(problems)
+        self.count = len(self.problems)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        arr = (Params * self.count)(*[make_params(p, precision, inner_tol, max_outer, device_loop)
+                                      for p in self.problems])
+        h = ctypes.c_void_p()
+        st = self.lib.rfnse_batch_create(arr, self.count, ctypes.c_void_p(self.stream.cuda_stream),
+                                         ctypes.byref(h))
+        if st != RFNSE_OK:
+            raise RfnseError(st, self.lib.rfnse_batch_last_error(None).decode())
+        self.h = h
+        self.ctx = [ctypes.c_void_p(self.lib.rfnse_batch_context(self.h, i)) for i in range(self.count)]
+        self.sizes = [int(self.lib.rfnse_size(c)) for c in self.ctx]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rfnse_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, ctx=None):
+        if st == RFNSE_OK:
+            return
+        msg = (self.lib.rfnse_last_error(ctx) if ctx is not None else self.lib.rfnse_batch_last_error(self.h)).decode()
+        if st == RFNSE_ENOCONV:
+            raise NoConvergence(st, msg)
+        raise RfnseError(st, msg)
+
+    def set_state(self, i: int, u_cur, u_prev=None, step: int = 0):
+        self._check(self.lib.rfnse_set_state(self.ctx[i], _ptr(u_prev) if u_prev is not None else None,
+                                             _ptr(u_cur), step, 1), self.ctx[i])
+
+    def get_state(self, i: int):
+        import torch
+        up = torch.empty(self.sizes[i], dtype=torch.complex128, device="cuda")
+        uc = torch.empty(self.sizes[i], dtype=torch.complex128, device="cuda")
+        step = ctypes.c_int()
+        self._check(self.lib.rfnse_get_state(self.ctx[i], _ptr(up), _ptr(uc), ctypes.byref(step), 1), self.ctx[i])
+        return up, uc, step.value
+
+    def run(self, nsteps: int, allow_noconv: bool = False):
+        """Advance every instance nsteps; returns (iters, relres) of shape (nsteps, count)."""
+        iters = np.zeros((max(nsteps, 1), self.count), dtype=np.int32)
+        relres = np.zeros((max(nsteps, 1), self.count), dtype=np.float64)
+        st = self.lib.rfnse_batch_run(self.h, nsteps, iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                      relres.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        if not (allow_noconv and st == RFNSE_ENOCONV):
+            self._check(st)
+        return iters[:nsteps], relres[:nsteps]
