@@ -22,10 +22,12 @@ Everything here follows the paper's own formulation, in its notation:
                    rotations (Sec. 5 protocol: zero initial guess, relative-residual stop).
 * ``scheme``    -- the three-level linearly implicit scheme (Sec. 2.1 eq. 'discretizedRFSE',
                    Sec. 2.2 eq. 'discretizedRFSE2D'), its first step, and the discrete mass/energy.
+* ``adjoint``   -- the reverse-mode gradient of that discrete scheme with respect to u^0 and rho
+                   (derived from the scheme; the paper has no adjoint), one conjugate solve per step.
 
 The oracle works on the REAL block vectors x = [z; y] of the paper (u = y + i z), not on complex
 vectors, so that the complex-arithmetic CUDA path and this oracle reach the same numbers by
 different routes.  Transforms and Toeplitz products are dense matrix products (the plain
 definitions); no FFT is used anywhere in the oracle.
 """
-from . import fcd, operators, tau, precond, gmres, scheme  # noqa: F401
+from . import fcd, operators, tau, precond, gmres, scheme, adjoint  # noqa: F401

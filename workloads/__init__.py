@@ -153,3 +153,26 @@ def config_batched(count: int = 64, seed: int = 2410, sizes=(127, 255, 511)):
                     dt=0.005, tol=1e-10)
         out.append((p, u0_sech_product(p, [kx, ky])))
     return out, 20
+
+
+def config_adjoint(n: int = 255):
+    """Gradient workload: d=2, n=255^2 on [-10,10]^2, alpha=1.5, rho=2, dt=0.005, 20 steps, FP64,
+    u0 = sech(x)sech(y)e^{i(x+y)}.  The target of L = sum |u(T) - u_target|^2 is the run from
+    u0 (1 + 0.01 xi) with rho * 1.05, xi complex normal (seed 3643).  Returns
+    (problem, u0, nsteps, u0_target, rho_target)."""
+    p = Problem(d=2, n=(n, n), lo=(-10.0, -10.0), hi=(10.0, 10.0), alpha=1.5, rho=2.0, dt=0.005,
+                tol=1e-10)
+    u0 = u0_sech_product(p, [1.0, 1.0])
+    xi = random_field(p.shape, 3643) / math.sqrt(2.0)
+    return p, u0, 20, u0 * (1.0 + 0.01 * xi), p.rho * 1.05
+
+
+def fd_directions(shape, count: int = 8, seed: int = 643):
+    """Seeded unit directions for finite-difference checks: `count` complex normal fields of the
+    given shape (normalised to unit 2-norm) and `count` scalar directions for rho."""
+    rng = np.random.default_rng(seed)
+    dirs = []
+    for _ in range(count):
+        v = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+        dirs.append((v / np.linalg.norm(v)).astype(np.complex128))
+    return dirs, rng.standard_normal(count)
