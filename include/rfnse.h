@@ -138,6 +138,39 @@ rfnse_ctx* rfnse_batch_context(rfnse_batch* b, int i);
    ENOCONV (every step is still taken), ENUMERIC, ETIMEOUT. */
 int rfnse_batch_run(rfnse_batch* b, int nsteps, int* iters, double* relres);
 
+/* ---- reverse pass: gradients of a loss of u^N ---------------------------------------------------
+ * The paper has no adjoint: these compute the exact derivative of its discrete scheme (eq.
+ * 'discretizedCNLSMaxForm' of Sec. 2.1, eq. 'discretizedRFSE2DMaxForm' of Sec. 2.2, and the
+ * first step as rfnse_run takes it).  For a real loss L the gradient of a complex grid function u is
+ * g = dL/dRe(u) + i dL/dIm(u) (so dL = Re(g^H du)), stored like u.  Each step of the reverse pass is
+ * one solve with the conjugate system matrix, M^{-H} g = conj(M^{-1} conj(g)) (M = D - T + iI is
+ * complex symmetric), by the same tau-preconditioned GMRES, plus one Toeplitz product. */
+
+/* Taped forward run: load u0 (step 0), take nsteps time steps exactly as rfnse_run, and keep u^0, the
+   final pair and the pair (u^{kC-1}, u^{kC}) at every multiple kC < nsteps of C = every (library-owned
+   device memory, about 2 nsteps / C + C + 8 grid vectors, kept until the context is destroyed and
+   reused by the next taped run).  u0: N complex FP64; uN (may be NULL): receives u^nsteps; both host
+   (on_device = 0) or device (1).  iters (host, may be NULL): nsteps counts.  On return the context
+   holds the final state, as after rfnse_run.  Errors: EINVAL, ENOMEM, ECUDA, ENOCONV (the run and
+   the tape are complete), ENUMERIC. */
+int rfnse_tape_forward(rfnse_ctx* ctx, const void* u0, int nsteps, int every, void* uN, int* iters,
+                       int on_device);
+
+/* Reverse pass of the last taped run: from gN = dL/du^N, compute g0 = dL/du^0 and *grho = dL/drho
+   (rho, dt, the grid and the first-step rule are the context's).  Each segment between checkpoints
+   is recomputed once from its checkpoint, so the pass costs about one forward step and one
+   conjugate solve per step.  gN, g0: N complex FP64, host (on_device = 0) or device (1), may not
+   alias; grho, iters (host, may be NULL): iters receives the total Arnoldi steps of the conjugate
+   solves.  On return the context holds the taped run's final state.  Errors: EINVAL (no taped run),
+   ECUDA, ENOCONV (a solve stopped at max_it; the gradient is still written), ENUMERIC. */
+int rfnse_tape_backward(rfnse_ctx* ctx, const void* gN, void* g0, double* grho, int* iters, int on_device);
+
+/* lam = (D - T + iI)^{-H} g: one conjugate solve (mu_a / 2 when half = 1) with the context's
+   tolerance and precision.  g, lam: N complex FP64 device values (may not alias); D: N FP64 device
+   values; iters, relres: host, may be NULL.  Errors: EINVAL, ENOMEM, ECUDA, ENOCONV, ENUMERIC. */
+int rfnse_adjoint_solve(rfnse_ctx* ctx, const double* D, const void* g, void* lam, int half, int* iters,
+                        double* relres);
+
 /* ---- building blocks (device pointers; used by the parity tests) ---------------------------- */
 
 /* out = (D - T + iI) u, the system matrix of eq. 'equ3' (Sec. 2).  half = 1 uses mu_a/2 (first

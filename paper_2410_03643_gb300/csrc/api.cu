@@ -74,6 +74,8 @@ void free_ctx(rfnse_ctx* c) {
   if (c->cap_stream2) cudaStreamDestroy(c->cap_stream2);
   cudaFree(c->bar);
   cudaFree(c->coop_partials);
+  cudaFree(c->tape);
+  cudaFree(c->adj_red);
   delete c;
 }
 

@@ -185,6 +185,13 @@ struct rfnse_ctx {
   cudaStream_t cap_stream2 = nullptr;  // private stream that captures a stand-alone solve graph
   cudaGraph_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   cudaGraphExec_t graph_exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  // reverse pass (adjoint.cu): the taped forward run and its work vectors
+  double2* keep_pred = nullptr;  // when set, the first time step copies its predictor here
+  double2* tape = nullptr;       // checkpoints, segment states and gradient vectors
+  size_t tape_vecs = 0;          // grid vectors allocated in tape
+  double* adj_red = nullptr;     // per-block partial sums of the rho gradient, then the running sum
+  int tape_steps = -1;           // steps of the taped run (-1: none)
+  int tape_every = 0;            // checkpoint interval of the taped run
   // per-step statistics of the last solve
   int last_iters = 0, last_outer = 0;
   double last_relres = 0.0;

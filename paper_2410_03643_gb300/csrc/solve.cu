@@ -596,6 +596,8 @@ rfnse_status time_step(rfnse_ctx* c, int* iters, double* relres) {
     if (st != RFNSE_OK && st != RFNSE_ENOCONV) return st;
     if (c->p.first_step == 1) {
       int it2 = 0;
+      if (c->keep_pred)  // the reverse pass reads the predictor
+        RFNSE_CUDA_TRY(c, cudaMemcpyAsync(c->keep_pred, un, sizeof(double2) * N, cudaMemcpyDeviceToDevice, c->stream));
       launch_diag(u0, un, c->D, rdt, N, c->stream);
       RFNSE_CUDA_TRY(c, run_matvec_fp64(c, u0, c->D, c->f, nullptr, kOne, kMinusI, 1, nullptr));
       st2 = solve_block(c, c->D, c->f, un, 1, &it2, relres);

@@ -54,7 +54,8 @@ EXPORTED = ("rfnse_default_params", "rfnse_create", "rfnse_destroy", "rfnse_last
             "rfnse_set_state", "rfnse_get_state", "rfnse_run", "rfnse_apply_A", "rfnse_apply_prec",
             "rfnse_dst", "rfnse_toeplitz", "rfnse_solve", "rfnse_get_coefficients", "rfnse_launch_count",
             "rfnse_profile", "rfnse_profile_read", "rfnse_probe_fma", "rfnse_batch_create",
-            "rfnse_batch_destroy", "rfnse_batch_last_error", "rfnse_batch_context", "rfnse_batch_run")
+            "rfnse_batch_destroy", "rfnse_batch_last_error", "rfnse_batch_context", "rfnse_batch_run",
+            "rfnse_tape_forward", "rfnse_tape_backward", "rfnse_adjoint_solve")
 
 K_INSCALE, K_DST, K_LAM, K_DSCALE, K_TOEP_X, K_TOEP_ACC, K_FP32 = 1, 2, 4, 8, 16, 32, 256
 
@@ -117,6 +118,12 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.rfnse_batch_context.restype = vp
     lib.rfnse_batch_run.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), dp]
     lib.rfnse_batch_run.restype = ip
+    lib.rfnse_tape_forward.argtypes = [vp, vp, ip, ip, vp, ctypes.POINTER(ctypes.c_int), ip]
+    lib.rfnse_tape_forward.restype = ip
+    lib.rfnse_tape_backward.argtypes = [vp, vp, vp, dp, ctypes.POINTER(ctypes.c_int), ip]
+    lib.rfnse_tape_backward.restype = ip
+    lib.rfnse_adjoint_solve.argtypes = [vp, vp, vp, vp, ip, ctypes.POINTER(ctypes.c_int), dp]
+    lib.rfnse_adjoint_solve.restype = ip
     if path == _build.library_path():
         _lib = lib
     return lib
@@ -279,6 +286,35 @@ class Solver:
                                          ctypes.byref(rr)))
         return u, it.value, rr.value
 
+    def adjoint_solve(self, D, g, half: bool = False):
+        """lam = (D - T + iI)^{-H} g; returns (lam, iters, relres)."""
+        import torch
+        lam = torch.empty_like(g)
+        it = ctypes.c_int()
+        rr = ctypes.c_double()
+        self._check(self.lib.rfnse_adjoint_solve(self.h, _ptr(D), _ptr(g), _ptr(lam), int(half), ctypes.byref(it),
+                                                 ctypes.byref(rr)))
+        return lam, it.value, rr.value
+
+    # -- reverse pass ------------------------------------------------------------------------
+    def tape_forward(self, u0, nsteps: int, every: int = 5):
+        """Taped run of nsteps from u0 (torch complex128 CUDA, N values): returns (u^N, iters)."""
+        import torch
+        uN = torch.empty_like(u0)
+        iters = np.zeros(max(nsteps, 1), dtype=np.int32)
+        self._check(self.lib.rfnse_tape_forward(self.h, _ptr(u0), nsteps, every, _ptr(uN),
+                                                iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), 1))
+        return uN, iters[:nsteps]
+
+    def tape_backward(self, gN):
+        """(dL/du^0, dL/drho, conjugate-solve Arnoldi steps) of the last taped run from gN = dL/du^N."""
+        import torch
+        g0 = torch.empty_like(gN)
+        grho = ctypes.c_double()
+        it = ctypes.c_int()
+        self._check(self.lib.rfnse_tape_backward(self.h, _ptr(gN), _ptr(g0), ctypes.byref(grho), ctypes.byref(it), 1))
+        return g0, grho.value, it.value
+
     def profile(self, kind: int):
         """Time every launch of kernel class `kind` (K_* flags; 0 = off)."""
         self._check(self.lib.rfnse_profile(self.h, kind))
@@ -361,3 +397,43 @@ class Batch:
         if not (allow_noconv and st == RFNSE_ENOCONV):
             self._check(st)
         return iters[:nsteps], relres[:nsteps]
+
+
+def _rollout_function():
+    import torch
+
+    class Rollout(torch.autograd.Function):
+        """u^N = scheme(u^0, rho) over nsteps time steps, differentiable in u^0 and rho.  The backward
+        is the library's reverse pass (one conjugate solve and one recomputed forward step per step)."""
+
+        @staticmethod
+        def forward(ctx, u0, rho, problem, nsteps, every, precision, device_loop):
+            solver = Solver(problem.replace(rho=float(rho)), precision=precision, device_loop=device_loop)
+            flat = u0.detach().reshape(-1).contiguous()
+            uN, _ = solver.tape_forward(flat, nsteps, every)
+            ctx.solver = solver
+            ctx.rho_meta = (rho.dtype, rho.device)
+            return uN.reshape(u0.shape)
+
+        @staticmethod
+        def backward(ctx, gN):
+            g0, grho, _ = ctx.solver.tape_backward(gN.reshape(-1).contiguous())
+            ctx.solver.close()
+            dtype, device = ctx.rho_meta
+            return (g0.reshape(gN.shape), torch.tensor(grho, dtype=dtype, device=device), None, None, None, None,
+                    None)
+
+    return Rollout
+
+
+_ROLLOUT = None
+
+
+def rollout(problem, u0, rho, nsteps: int, every: int = 5, precision: int = 0, device_loop: int = 1):
+    """Differentiable time stepping: u^N from u0 (complex128 CUDA tensor of the grid's N values, any
+    shape) and rho (a 0-d float64 tensor, may require grad); problem gives everything else.
+    Gradients follow torch's convention for complex tensors (dL/dRe + i dL/dIm for a real loss)."""
+    global _ROLLOUT
+    if _ROLLOUT is None:
+        _ROLLOUT = _rollout_function()
+    return _ROLLOUT.apply(u0, rho, problem, nsteps, every, precision, device_loop)
