@@ -7,7 +7,12 @@ instances by one time step (a GMRES solve each) in the mixed form (FP32 transfor
 FP64 Arnoldi/Givens and FP64 outer residual); the plain FP64 form is timed the same way and reported
 beside it, with the difference between the two trajectories.  DOF = complex grid unknowns.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload 2d|3d|1d]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload 2d|3d|1d|batched|adjoint]
+
+Other workloads: 3d (255^3, mixed), 1d (n = 1023), batched (64 independent 2-D instances with grids
+drawn from {127, 255, 511}^2: one step = one graph launch advancing all of them), adjoint (255^2,
+20 steps, FP64: one step = a taped forward run plus its reverse pass, dL/du0 and dL/drho).
 
 Multi-GPU (torchrun): every rank advances its own copy of the three instances (independent problems,
 no collective on the data path; weak scaling); value = all ranks' DOF x steps / max rank time.
@@ -46,11 +51,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d", choices=["2d", "3d", "1d", "batched"])
+    ap.add_argument("--workload", default="2d", choices=["2d", "3d", "1d", "batched", "adjoint"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--serial", action="store_true", help="advance the instances one after another on one stream")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive the GMRES loops from the host (no CUDA graphs; same kernels, for kernel profilers)")
     ap.add_argument("--alu-probe", action="store_true",
                     help="only measure the FP64 and FP32 FMA rates of the GPU and print them")
     return ap.parse_args()
@@ -250,7 +257,9 @@ def run_ours(args):
     concurrent = not args.serial and len(inst) > 1
     pool = ThreadPoolExecutor(max_workers=len(inst)) if concurrent else None
 
-    def make(precision, device_loop=1):
+    def make(precision, device_loop=None):
+        if device_loop is None:
+            device_loop = 0 if args.host_loop else 1
         solvers = []
         for p, u0 in inst:
             st = torch.cuda.Stream(device=dev) if concurrent else main
@@ -343,7 +352,9 @@ def run_ours(args):
                           l2="256 MiB buffer written between timed steps",
                           parallelism=(f"{world} GPU(s), instances replicated per GPU; "
                                        + ("one CUDA stream and host thread per instance" if concurrent
-                                          else "instances in turn on one stream"))),
+                                          else "instances in turn on one stream")),
+                          control=("host-driven GMRES loops" if args.host_loop
+                                   else "device-decided GMRES loops, one CUDA graph per solve")),
            "gpu_launches": launches,
            "iters_per_solve_mean": float(np.mean(iters_m)) if iters_m else None}
 
@@ -511,6 +522,77 @@ def run_batched(args):
         dist.destroy_process_group()
 
 
+def run_adjoint(args):
+    """The gradient workload (255^2, 20 steps, FP64): one bench step = a taped forward run plus its
+    reverse pass (dL/du0 and dL/drho of L = sum |u^N - u_target|^2), checkpoints every 5 steps."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2410_03643_gb300 import build, rfnse
+    build.build_library()
+    p, u0, nsteps, u0t, rho_t = W.config_adjoint()
+    main = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    st = rfnse.Solver(p.replace(rho=rho_t), precision=0, stream=main)
+    target, _ = st.tape_forward(torch.from_numpy(u0t.ravel().copy()).to(dev), nsteps, 5)
+    st.close()
+    s = rfnse.Solver(p, precision=0, stream=main)
+    x0 = torch.from_numpy(u0.ravel().copy()).to(dev)
+
+    def one():
+        uN, _ = s.tape_forward(x0, nsteps, 5)
+        return s.tape_backward(2.0 * (uN - target))
+
+    for _ in range(max(args.warmup, 3)):
+        one()
+    torch.cuda.synchronize()
+    l0 = rfnse.launch_count()
+    fw, bw = [], []
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        clocks.mark_on()
+    barrier(world)
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(main)
+        uN, _ = s.tape_forward(x0, nsteps, 5)
+        e1.record(main)
+        g0, grho, its = s.tape_backward(2.0 * (uN - target))
+        e2.record(main)
+        torch.cuda.synchronize()
+        fw.append(e0.elapsed_time(e1))
+        bw.append(e1.elapsed_time(e2))
+    if clocks:
+        clocks.mark_off()
+    clk = clocks.stop() if clocks else None
+    launches = rfnse.launch_count() - l0
+    ms = reduce_max(sum(fw) + sum(bw), world, dev)
+    out = {"metric": METRIC, "value": world * p.size * nsteps * args.steps / (ms * 1e-3), "unit": UNIT,
+           "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (closed-form initial data; target from a seeded perturbation of u0 and rho)",
+           "config": {"workload": "adjoint_2d_n255_alpha1.5_rho2_dt0.005_20steps_fp64", "d": 2, "n": [255, 255],
+                      "what": "one step = taped forward run + reverse pass (dL/du0, dL/drho), checkpoint every 5",
+                      "l2": "256 MiB buffer written between timed steps", "parallelism": f"{world} GPU(s)"},
+           "gpu_launches": launches, "forward_ms": sum(fw) / args.steps, "backward_ms": sum(bw) / args.steps,
+           "backward_over_forward": sum(bw) / max(sum(fw), 1e-9), "adjoint_arnoldi_steps": its,
+           "grad_rho": grho}
+    if clk:
+        out["clocks"] = clk
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    s.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def alu_probe():
     import torch
     from paper_2410_03643_gb300 import build, rfnse
@@ -531,6 +613,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 

@@ -188,6 +188,8 @@ __global__ void __launch_bounds__(kCtlThreads) k_norm_ctl(const double2* __restr
   unsigned cont;
   if (mode == 0) {
     gs->fnorm = b;
+    gs->upd = 0;
+    gs->upd_err = 0.0;
     gs->it = 0;
     gs->outer = 0;
     gs->err = 0;
@@ -199,11 +201,12 @@ __global__ void __launch_bounds__(kCtlThreads) k_norm_ctl(const double2* __restr
   } else {
     gs->outer += 1;
     const double rel = b / gs->fnorm;
+    const double margin = (mode == 2 && gs->upd) ? gs->upd_err : 0.0;  // recurrence residual: its error bound
     gs->relres = rel;
     if (!isfinite(b)) {
       gs->done = 3;
       cont = 0u;
-    } else if (rel < cfg.tol) {
+    } else if (rel + margin < cfg.tol) {
       gs->done = 1;
       cont = 0u;
     } else {
@@ -263,6 +266,57 @@ __global__ void k_combine_dev(const double2* __restrict__ V, long long ldv, cons
       a.y += y[q] * v.y;
     }
     out[i] = a;
+  }
+}
+
+// Mixed form, end of a refinement cycle: the residual recurrence.  The flexible Arnoldi relation
+// R Z_k = V_{k+1} Hbar_k (products R z_j in FP32, basis and Hessenberg matrix in FP64) gives
+//   r_new = r_old - R Z_k y = V_{k+1} (beta e_1 - Hbar_k y) = V_{k+1} Q_k^T (g_k e_k),
+// i.e. the Givens rotations undone on the last residual estimate g_k, up to the FP32 error of the
+// products, about kUpdErr ||Z_k y|| <= kUpdErr beta (||R^{-1}|| <= 1: R = I + i(T - D), T - D real
+// symmetric).  Used only when beta <= kUpdRatio tol ||f||, so that this error stays a small fraction
+// of tol ||f||; it is also added to the stopping test.  k < 0: k = gs->j and the decision is taken
+// here; otherwise upd and err come from the host.
+__global__ void k_resid_coeffs(GmresState* gs, int k_in, int upd_in, double err_in, double tol) {
+  const int k = k_in >= 0 ? k_in : gs->j;
+  int upd;
+  double err;
+  if (k_in >= 0) {
+    upd = upd_in;
+    err = err_in;
+  } else {
+    upd = (gs->outer >= 1 && gs->beta <= kUpdRatio * tol * gs->fnorm) ? 1 : 0;
+    err = kUpdErr * gs->beta / gs->fnorm;
+  }
+  gs->upd = upd;
+  gs->upd_err = upd ? err : 0.0;
+  if (!upd) return;
+  double t = gs->g[k];
+  for (int i = k - 1; i >= 0; --i) {
+    gs->q[i + 1] = gs->cs[i] * t;
+    t = -gs->sn[i] * t;
+  }
+  gs->q[0] = t;
+}
+
+// r = sum_{i<k} q_i V_i + q_k inv_h w when gs->upd, k = gs->j if k_in < 0.
+__global__ void k_resid_update(const double2* __restrict__ V, long long ldv, const double2* __restrict__ w,
+                               const GmresState* gs, int k_in, double2* __restrict__ r, long long N) {
+  if (!gs->upd) return;  // uniform
+  __shared__ double q[kMaxM + 1];
+  const int k = k_in >= 0 ? k_in : gs->j;
+  if (threadIdx.x <= k) q[threadIdx.x] = gs->q[threadIdx.x];
+  __syncthreads();
+  const double cw = (q[k] == 0.0) ? 0.0 : q[k] * gs->inv_h;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double2 wv = w[i];
+    double2 a = make_double2(cw * wv.x, cw * wv.y);
+    for (int j = 0; j < k; ++j) {
+      const double2 v = V[(size_t)j * ldv + i];
+      a.x += q[j] * v.x;
+      a.y += q[j] * v.y;
+    }
+    r[i] = a;
   }
 }
 
@@ -380,6 +434,15 @@ void launch_combine_f32_add_dev(const float2* Z, long long ldz, const GmresState
                                 cudaStream_t s) {
   count_launch();
   k_combine_f32_add_dev<<<ew_blocks_c(N), 256, 0, s>>>(Z, ldz, gs, x, N);
+}
+void launch_resid_coeffs(GmresState* gs, int k, int upd, double err, double tol, cudaStream_t s) {
+  count_launch();
+  k_resid_coeffs<<<1, 1, 0, s>>>(gs, k, upd, err, tol);
+}
+void launch_resid_update(const double2* V, long long ldv, const double2* w, const GmresState* gs, int k,
+                         double2* r, long long N, cudaStream_t s) {
+  count_launch();
+  k_resid_update<<<ew_blocks_c(N), 256, 0, s>>>(V, ldv, w, gs, k, r, N);
 }
 
 }  // namespace rfnse

@@ -37,9 +37,11 @@ struct GmresState {
   const double2* src;  // vector that starts the next Arnoldi column (r or w) ...
   double src_scale;    // ... and the factor that normalises it (1/beta or 1/h)
   int no_restart;   // 1 when the cycle ended converged or out of iterations (restart kernels skip)
-  int pad2_;
+  int upd;          // mixed form: 1 when this cycle's residual is formed from the Arnoldi basis
+  double upd_err;   // ... and a bound on that residual's relative error (added to the stopping test)
   double H[(kMaxM + 1) * kMaxM];
   double cs[kMaxM], sn[kMaxM], g[kMaxM + 1], y[kMaxM];
+  double q[kMaxM + 1];  // residual coefficients: r = sum_i q_i v_i (v_k = w / h_{k,k-1})
 };
 
 // Host-visible copy of the prefix of GmresState that the control loop reads.
@@ -76,6 +78,16 @@ void launch_norm_ctl(const double2* x, GmresState* gs, long long N, int blocks, 
 void launch_cycle_begin(GmresState* gs, const SolveCfg& cfg, cudaGraphConditionalHandle h_inner,
                         cudaGraphConditionalHandle h_outer, int set_cond, cudaStream_t s);
 void launch_backsolve_dev(GmresState* gs, cudaStream_t s);
+// Mixed form, end of a refinement cycle of k Arnoldi steps (k < 0: gs->j).  Decides whether the new
+// residual is formed from the Arnoldi basis (upd < 0: on the device, when the cycle's starting
+// residual beta <= kUpdRatio * tol * ||f||; otherwise upd as given) and, if so, stores its
+// coefficients q = Q^T g_k e_k (the Givens rotations undone on the last residual estimate).
+constexpr double kUpdRatio = 1e5;
+constexpr double kUpdErr = 4e-7;  // relative error of an FP32 product, times beta / ||f||: the bound
+void launch_resid_coeffs(GmresState* gs, int k, int upd, double err, double tol, cudaStream_t s);
+// r = sum_{i<k} q_i V_i + q_k inv_h w when gs->upd (else nothing); k < 0: gs->j
+void launch_resid_update(const double2* V, long long ldv, const double2* w, const GmresState* gs, int k,
+                         double2* r, long long N, cudaStream_t s);
 void launch_tu_from_residual_dev(const GmresState* gs, const double* D, const double2* f, const double2* x,
                                  const double2* r, double2* Tu, long long N, cudaStream_t s);
 void launch_gather_peeks(GmresState* const* gs, GmresPeek* out, int count, cudaStream_t s);

@@ -285,7 +285,10 @@ void launch_start_cycle(GmresState* gs, double ref, double tol, cudaStream_t s) 
   count_launch();
   k_start_cycle<<<1, 1, 0, s>>>(gs, ref, tol);
 }
-void launch_backsolve(GmresState* gs, int k, cudaStream_t s) { k_backsolve<<<1, 1, 0, s>>>(gs, k); }
+void launch_backsolve(GmresState* gs, int k, cudaStream_t s) {
+  count_launch();
+  k_backsolve<<<1, 1, 0, s>>>(gs, k);
+}
 void launch_combine(const double2* V, long long ldv, const GmresState* gs, int k, double2* out, long long N,
                     cudaStream_t s) {
   count_launch();

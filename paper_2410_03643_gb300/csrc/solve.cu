@@ -323,10 +323,11 @@ static rfnse_status solve_mixed(rfnse_ctx* c, const double* D, const double2* f,
   if (fnorm == 0.0) return RFNSE_OK;
   const double2* r = f;
   double beta = fnorm;
+  double margin = 0.0;  // error bound of a residual formed by the recurrence
   int it = 0, outer = 0;
   for (;;) {
     *relres = beta / fnorm;
-    if (beta / fnorm < tol) break;
+    if (beta / fnorm + margin < tol) break;
     if (outer >= max_outer || it >= c->p.max_it) {
       *iters = it;
       *outer_out = outer;
@@ -353,8 +354,18 @@ static rfnse_status solve_mixed(rfnse_ctx* c, const double* D, const double2* f,
     }
     launch_backsolve(c->gs, k, c->stream);
     launch_combine_f32_add(c->Z32, N, c->gs, k, x, N, c->stream);
+    // the new residual: FP64 product after the first cycle and while beta is large, else the
+    // recurrence from the Arnoldi basis (k_resid_coeffs)
+    const int upd = (outer >= 1 && beta <= kUpdRatio * tol * fnorm) ? 1 : 0;
+    margin = upd ? kUpdErr * beta / fnorm : 0.0;
     ++outer;
-    RFNSE_CUDA_TRY(c, run_matvec_fp64(c, x, D, c->r, f, kMinusOne, kMinusI, half, nullptr));
+    if (upd) {
+      launch_resid_coeffs(c->gs, k, 1, margin, tol, c->stream);
+      launch_resid_update(c->V, N, c->w, c->gs, k, c->r, N, c->stream);
+    } else {
+      launch_resid_coeffs(c->gs, k, 0, 0.0, tol, c->stream);
+      RFNSE_CUDA_TRY(c, run_matvec_fp64(c, x, D, c->r, f, kMinusOne, kMinusI, half, nullptr));
+    }
     launch_norm(c->r, c->gs, N, c->red_blocks, c->partials, c->counter, c->stream);
     if ((st = peek(c, &pk))) return st;
     beta = pk.beta;
@@ -462,8 +473,10 @@ cudaError_t capture_solve(rfnse_ctx* c, int mixed, int half, cudaGraph_t g, cuda
   launch_backsolve_dev(c->gs, bs);
   if (mixed) {
     launch_combine_f32_add_dev(c->Z32, N, c->gs, c->x, N, bs);
-    if ((e = run_matvec_fp64(c, c->x, c->D, c->r, c->f, kMinusOne, kMinusI, half, nullptr)) != cudaSuccess)
+    launch_resid_coeffs(c->gs, -1, -1, 0.0, cfg.tol, bs);
+    if ((e = run_matvec_fp64(c, c->x, c->D, c->r, c->f, kMinusOne, kMinusI, half, &c->gs->upd)) != cudaSuccess)
       return fail(e);
+    launch_resid_update(c->V, N, c->w, c->gs, -1, c->r, N, bs);
     launch_norm_ctl(c->r, c->gs, N, c->red_blocks, c->partials, c->counter, c->bar, cfg, 2, ho, 1, bs);
   } else {
     launch_combine_dev(c->V, N, c->gs, c->r, N, bs);
@@ -535,7 +548,7 @@ static rfnse_status solve_graph(rfnse_ctx* c, const double* D, const double2* f,
      // per cycle the cycle start, back-substitution, update and residual kernels
     const int d = c->d;
     const long long step_k = (d == 1 ? 1 : 3 * d - 2) + 1;
-    const long long cycle_k = mixed ? 1 + 1 + 1 + d + 1 : 1 + 1 + 1 + (d == 1 ? 1 : 2 * d - 1) + d + 1;
+    const long long cycle_k = mixed ? 1 + 1 + 1 + 1 + d + 1 + 1 : 1 + 1 + 1 + (d == 1 ? 1 : 2 * d - 1) + d + 1;
     const long long cycles = mixed ? pk.outer : (pk.it > 0 ? pk.outer + 1 : 0);
     count_launch(2 + step_k * pk.it + cycle_k * cycles);
   }
