@@ -43,6 +43,20 @@ UNIT = "DOF*timesteps/s"
 FP64_ALU_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP64 Toeplitz x-pass (ncu)
 TRAFFIC_FP64_TOEP_X = {"2d": 10530816 + 0}
+FP32_ALU_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9  # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
+
+
+def measured_hbm_gbs():
+    """The machine's measured copy bandwidth (MEASURED_PEAKS.json), else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+# DRAM read+write per launch of the FP32 fused DST-x + (wI+D) + Toeplitz-x pass (ncu, 2-D 511^2)
+TRAFFIC_FP32_FUSED_X = {"2d": 5288192 + 0}
 
 
 def parse():
@@ -336,11 +350,19 @@ def run_ours(args):
     # (in the concurrent region the instances' kernels share the SMs, which stretches each launch)
     # (host-driven solvers: CUDA events cannot be recorded around single kernels inside a running graph;
     # the kernels are the same as in the device loop)
+    nprof = max(1, min(args.steps, 20))
     prof_solvers = make(1, device_loop=0)
-    ms_r, _, _, _, prof = timed(prof_solvers, max(1, min(args.steps, 20)), args.warmup, profile_kind=dom_kind,
-                                serial=True)
+    ms_r, _, _, _, prof = timed(prof_solvers, nprof, args.warmup, profile_kind=dom_kind, serial=True)
     for s in prof_solvers:
         s.close()
+    # the other large class: the FP32 pass that ends the preconditioner and starts the product along x
+    prof32 = None
+    if args.workload in ("2d", "3d"):
+        k32 = rfnse.K_FP32 | rfnse.K_DST | rfnse.K_DSCALE | rfnse.K_TOEP_X
+        prof_solvers = make(1, device_loop=0)
+        ms_r32, _, _, _, prof32 = timed(prof_solvers, nprof, args.warmup, profile_kind=k32, serial=True)
+        for s in prof_solvers:
+            s.close()
     ms_max = reduce_max(ms, world, dev)
     value = world * dof_per_step * args.steps / (ms_max * 1e-3)
 
@@ -358,23 +380,46 @@ def run_ours(args):
            "gpu_launches": launches,
            "iters_per_solve_mean": float(np.mean(iters_m)) if iters_m else None}
 
-    # roofline of the dominant kernel class (FP64 Toeplitz pass along x of the outer residual)
+    # roofline of the two largest kernel classes, each timed launch by launch; the larger is `roofline`
+    measured = ("CUDA events around every launch of the class (on its stream), serial run of "
+                f"{nprof} further bench steps")
+    entries = []
     if prof and prof[0] > 0:
         n, pms, fl, by = prof
         achieved = fl / (pms * 1e-3) / 1e12
         peak = FP64_ALU_PEAK_FLOPS / 1e12
-        out["roofline"] = {"bound": "alu", "kernel": "k_line_pass<double,F_TOEP_X> (FP64 Toeplitz x-pass)",
-                           "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                           # DRAM read+write of one launch of this kernel, ncu capture of the current
-                           # code on the 2-D 511^2 workload (profiles/k_line_pass_fp64_toeplitz_x_2d511.md)
-                           "traffic": TRAFFIC_FP64_TOEP_X.get(args.workload), "launches": n,
-                           "avg_launch_us": 1e3 * pms / n,
-                           "share_of_step_time": pms / ms_r if ms_r > 0 else None,
-                           "measured": "CUDA events around every launch of the class, serial run of "
-                                       f"{max(1, min(args.steps, 20))} further bench steps",
-                           "algorithmic_bytes_per_launch": by / n,
-                           "achieved_GBps": by / (pms * 1e-3) / 1e9,
-                           "peak_note": "FP64 FMA peak 152 SM x 2 FMA/clk x 2.07 GHz (derived; measured 1.19 TFLOP/s at 1.995 GHz)"}
+        entries.append({"bound": "alu", "kernel": "k_line_pass<double,F_TOEP_X> (FP64 Toeplitz x-pass)",
+                        "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                        # DRAM read+write of one launch, ncu on the 2-D 511^2 workload
+                        # (profiles/k_line_pass_fp64_toeplitz_x_2d511.md)
+                        "traffic": TRAFFIC_FP64_TOEP_X.get(args.workload), "launches": n,
+                        "avg_launch_us": 1e3 * pms / n, "total_ms": pms,
+                        "share_of_step_time": pms / ms_r if ms_r > 0 else None, "measured": measured,
+                        "algorithmic_flops_per_launch": fl / n, "algorithmic_bytes_per_launch": by / n,
+                        "achieved_GBps": by / (pms * 1e-3) / 1e9,
+                        "peak_note": "FP64 FMA peak 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz (derived from "
+                                     "the measured 2 FP64 FMA/clk/SM: 1.19 TFLOP/s at 1.995 GHz)"})
+    if prof32 and prof32[0] > 0:
+        n, pms, fl, by = prof32
+        hbm, how = measured_hbm_gbs()
+        achieved = by / (pms * 1e-3) / 1e9
+        entries.append({"bound": "hbm", "kernel": "k_line_pass<float,F_DST|F_DSCALE|F_TOEP_X> "
+                                                  "(FP32 inverse DST x + (wI+D) + Toeplitz x)",
+                        "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                        # profiles/k_line_pass_fp32_fused_x_2d511.md
+                        "traffic": TRAFFIC_FP32_FUSED_X.get(args.workload), "launches": n,
+                        "avg_launch_us": 1e3 * pms / n, "total_ms": pms,
+                        "share_of_step_time": pms / ms_r32 if ms_r32 > 0 else None, "measured": measured,
+                        "algorithmic_flops_per_launch": fl / n, "algorithmic_bytes_per_launch": by / n,
+                        "achieved_TFLOPs": fl / (pms * 1e-3) / 1e12,
+                        "frac_of_fp32_alu_peak": fl / (pms * 1e-3) / FP32_ALU_PEAK_FLOPS,
+                        "peak_note": f"copy bandwidth, {how} (MEASURED_PEAKS.json); arithmetic intensity "
+                                     f"{fl / by:.1f} flop/B is below the FP32 balance point"})
+    if entries:
+        entries.sort(key=lambda e: -e["total_ms"])
+        out["roofline"] = entries[0]
+        if len(entries) > 1:
+            out["roofline_second"] = entries[1]
     if clk:
         out["clocks"] = clk
 
