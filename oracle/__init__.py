@@ -22,6 +22,8 @@ Everything here follows the paper's own formulation, in its notation:
                    rotations (Sec. 5 protocol: zero initial guess, relative-residual stop).
 * ``scheme``    -- the three-level linearly implicit scheme (Sec. 2.1 eq. 'discretizedRFSE',
                    Sec. 2.2 eq. 'discretizedRFSE2D'), its first step, and the discrete mass/energy.
+* ``circulant`` -- the comparators of Sec. 5: Strang's circulant TBAN preconditioner F_C (C-GMRES)
+                   and no preconditioner (GMRES).
 * ``adjoint``   -- the reverse-mode gradient of that discrete scheme with respect to u^0 and rho
                    (derived from the scheme; the paper has no adjoint), one conjugate solve per step.
 
@@ -30,4 +32,4 @@ vectors, so that the complex-arithmetic CUDA path and this oracle reach the same
 different routes.  Transforms and Toeplitz products are dense matrix products (the plain
 definitions); no FFT is used anywhere in the oracle.
 """
-from . import fcd, operators, tau, precond, gmres, scheme, adjoint  # noqa: F401
+from . import fcd, operators, tau, precond, circulant, gmres, scheme, adjoint  # noqa: F401

@@ -34,7 +34,7 @@ from __future__ import annotations
 import numpy as np
 
 from .operators import (ToeplitzOperator, diag_D, block_R_apply, rhs_block, block_to_complex)
-from .precond import TauTBANPreconditioner
+from .circulant import make_preconditioner
 from .gmres import gmres_right, GmresResult
 
 
@@ -45,8 +45,9 @@ class SchemeOracle:
         self.p = problem
         self.T = ToeplitzOperator(problem, 1.0)
         self.T_half = ToeplitzOperator(problem, 0.5)
-        self.P = TauTBANPreconditioner(problem, problem.omega, 1.0)
-        self.P_half = TauTBANPreconditioner(problem, problem.omega, 0.5)
+        # the sine-transform TBAN preconditioner (Sec. 4), or a comparator of Sec. 5 (problem.precond)
+        self.P = make_preconditioner(problem, problem.omega, 1.0)
+        self.P_half = make_preconditioner(problem, problem.omega, 0.5)
 
     # -- one linear system --------------------------------------------------------------------
     def rhs(self, T: ToeplitzOperator, D: np.ndarray, u_old: np.ndarray) -> np.ndarray:

@@ -39,6 +39,7 @@ class Problem:
     max_it: int = 2000
     tol: float = 1e-10
     first_step: int = 1  # 1 = predictor-corrector half step, 0 = predictor only
+    precond: int = 0     # 0 = sine-transform (tau) TBAN, 1 = Strang-circulant TBAN, 2 = none
 
     def h(self, a: int) -> float:
         return (self.hi[a] - self.lo[a]) / (self.n[a] + 1)
