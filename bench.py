@@ -8,11 +8,12 @@ FP64 Arnoldi/Givens and FP64 outer residual); the plain FP64 form is timed the s
 beside it, with the difference between the two trajectories.  DOF = complex grid unknowns.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload 2d|3d|1d|batched|adjoint]
+                  [--workload 2d|3d|1d|batched|adjoint|comparators]
 
 Other workloads: 3d (255^3, mixed), 1d (n = 1023), batched (64 independent 2-D instances with grids
 drawn from {127, 255, 511}^2: one step = one graph launch advancing all of them), adjoint (255^2,
-20 steps, FP64: one step = a taped forward run plus its reverse pass, dL/du0 and dL/drho).
+20 steps, FP64: one step = a taped forward run plus its reverse pass, dL/du0 and dL/drho),
+comparators (255^2: the same run with the sine-transform preconditioner, Strang's circulant and none).
 
 Multi-GPU (torchrun): every rank advances its own copy of the three instances (independent problems,
 no collective on the data path; weak scaling); value = all ranks' DOF x steps / max rank time.
@@ -65,7 +66,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d", choices=["2d", "3d", "1d", "batched", "adjoint"])
+    ap.add_argument("--workload", default="2d", choices=["2d", "3d", "1d", "batched", "adjoint", "comparators"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
@@ -638,6 +639,52 @@ def run_adjoint(args):
         dist.destroy_process_group()
 
 
+def run_comparators(args):
+    """tau-GMRES against the comparators of Sec. 5 (C-GMRES with Strang's circulant, plain GMRES) on
+    the same time-stepping run: 2-D 255^2, alpha = 1.5, rho = 2, dt = 0.005, tol 1e-10, mixed form."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2410_03643_gb300 import build, rfnse
+    build.build_library()
+    p, u0, _ = W.config_2d(1.5, n=255)
+    main = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {}
+    for pc, name in ((0, "tau-GMRES"), (1, "C-GMRES"), (2, "GMRES")):
+        q = p.replace(precond=pc, restart=256 if pc == 2 else p.restart)
+        s = rfnse.Solver(q, precision=1, stream=main)
+        s.set_state(torch.from_numpy(u0.ravel().copy()).to(dev))
+        s.run(max(args.warmup, 3))
+        steps = args.steps if pc != 2 else max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        ms, its = 0.0, []
+        for k in range(steps):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(main)
+            it, _ = s.run(1)
+            b.record(main)
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+            its.append(int(it[0]))
+        res[name] = {"value": q.size * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                     "iters_per_solve_mean": float(np.mean(its)), "steps": steps}
+        s.close()
+    out = {"metric": METRIC, "value": res["tau-GMRES"]["value"], "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": res["tau-GMRES"]["ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
+           "data": "synthetic (closed-form initial data of the paper's shape)",
+           "config": {"workload": "comparators_2d_n255_alpha1.5_rho2_dt0.005_tol1e-10", "d": 2, "n": [255, 255],
+                      "what": "the same run with the sine-transform preconditioner, Strang's circulant "
+                              "(Bluestein DFTs) and none (restart 256)",
+                      "l2": "256 MiB buffer written between timed steps"},
+           "comparators": res}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def alu_probe():
     import torch
     from paper_2410_03643_gb300 import build, rfnse
@@ -660,6 +707,8 @@ def main():
         run_batched(args)
     elif args.workload == "adjoint":
         run_adjoint(args)
+    elif args.workload == "comparators":
+        run_comparators(args)
     else:
         run_ours(args)
 

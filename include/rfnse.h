@@ -52,7 +52,7 @@ typedef struct {
   double rho;         /* nonlinearity strength, >= 0 */
   double dt;          /* time step, > 0 */
   double omega;       /* TBAN iteration parameter of the preconditioner, > 0 (the paper fixes 1) */
-  int restart;        /* GMRES restart length m, 1..64 */
+  int restart;        /* GMRES restart length m, 1..256 */
   int max_it;         /* maximum Arnoldi steps per linear solve (the paper uses 2000) */
   double tol;         /* stop when the relative residual ||f - R x|| / ||f|| < tol */
   int precision;      /* 0 = FP64 throughout; 1 = mixed: FP32 transforms inside an FGMRES inner
@@ -62,10 +62,16 @@ typedef struct {
   int max_outer;      /* mixed form: maximum refinement steps per solve (<= 0: 30) */
   int device_loop;    /* 1 = each solve is one CUDA graph whose conditional loops are decided on the
                          device (no host round trip per Arnoldi step); 0 = host-driven loop */
+  int precond;        /* preconditioner of every GMRES solve:
+                         0 = the sine-transform TBAN preconditioner F_tau (Sec. 4 eq. 'taupre');
+                         1 = the circulant TBAN preconditioner F_C of Sec. 5 ("C-GMRES"): tau(T) replaced
+                             by the Kronecker sum of Strang's circulant approximations of mu_a T_0;
+                         2 = none (plain GMRES, the paper's "GMRES" column) */
 } rfnse_params;
 
 /* Fill p with defaults: d=1, n=255, box [-20,20], alpha=1.5, rho=2, dt=0.01, omega=1, restart=20,
-   max_it=2000, tol=1e-10, precision=0, first_step=1, inner_tol=1e-6, max_outer=30, device_loop=1. */
+   max_it=2000, tol=1e-10, precision=0, first_step=1, inner_tol=1e-6, max_outer=30, device_loop=1,
+   precond=0. */
 void rfnse_default_params(rfnse_params* p);
 
 /* Create a solver context for the problem p (Sec. 2: grid, alpha, rho, dt) on the current CUDA

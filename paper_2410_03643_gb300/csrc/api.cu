@@ -76,6 +76,17 @@ void free_ctx(rfnse_ctx* c) {
   cudaFree(c->coop_partials);
   cudaFree(c->tape);
   cudaFree(c->adj_red);
+  for (int a = 0; a < 3; ++a) {
+    cudaFree(c->lamC[a]);
+    cudaFree(c->chirp64[a]);
+    cudaFree(c->chirp32[a]);
+    cudaFree(c->bspec64[a]);
+    cudaFree(c->bspec32[a]);
+  }
+  for (int h = 0; h < 2; ++h) {
+    cudaFree(c->lamfacC64[h]);
+    cudaFree(c->lamfacC32[h]);
+  }
   delete c;
 }
 
@@ -91,11 +102,12 @@ const char* validate(const rfnse_params* p) {
   if (!(p->rho >= 0.0) || !std::isfinite(p->rho)) return "rho must be finite and >= 0";
   if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return "dt must be finite and > 0";
   if (!(p->omega > 0.0) || !std::isfinite(p->omega)) return "omega must be finite and > 0";
-  if (p->restart < 1 || p->restart > kMaxM) return "restart must be in 1..64";
+  if (p->restart < 1 || p->restart > kMaxM) return "restart must be in 1..256";
   if (p->max_it < 1) return "max_it must be >= 1";
   if (!(p->tol > 0.0)) return "tol must be > 0";
   if (p->precision != 0 && p->precision != 1) return "precision must be 0 (FP64) or 1 (mixed)";
   if (p->first_step != 0 && p->first_step != 1) return "first_step must be 0 or 1";
+  if (p->precond < 0 || p->precond > 2) return "precond must be 0 (tau), 1 (Strang circulant) or 2 (none)";
   return nullptr;
 }
 
@@ -126,6 +138,7 @@ void rfnse_default_params(rfnse_params* p) {
   p->inner_tol = 1e-6;
   p->max_outer = 30;
   p->device_loop = 1;
+  p->precond = 0;
 }
 
 int rfnse_create(const rfnse_params* p, void* stream, rfnse_ctx** out) {
@@ -199,6 +212,19 @@ int rfnse_create(const rfnse_params* p, void* stream, rfnse_ctx** out) {
       chk(dalloc(&c->circ32s[h][a], c->L[a]));
     }
   }
+  if (p->precond == 1) {
+    for (int a = 0; a < c->d; ++a) {
+      chk(dalloc(&c->lamC[a], c->n[a]));
+      chk(dalloc(&c->chirp64[a], c->n[a]));
+      chk(dalloc(&c->chirp32[a], c->n[a]));
+      chk(dalloc(&c->bspec64[a], c->L[a]));
+      chk(dalloc(&c->bspec32[a], c->L[a]));
+    }
+    for (int h = 0; h < 2; ++h) {
+      chk(dalloc(&c->lamfacC64[h], N));
+      chk(dalloc(&c->lamfacC32[h], N));
+    }
+  }
   c->red_blocks = choose_reduce_blocks(N);
   c->use_graphs = p->device_loop != 0;
   c->coop_blocks = coop_blocks_for(N);
@@ -222,13 +248,21 @@ int rfnse_create(const rfnse_params* p, void* stream, rfnse_ctx** out) {
   chk(cudaMemsetAsync(c->u[0], 0, sizeof(double2) * N, c->stream));
   chk(cudaMemsetAsync(c->u[1], 0, sizeof(double2) * N, c->stream));
   launch_setup_coefficients(c->c, nmax, p->alpha, c->stream);
-  for (int a = 0; a < c->d; ++a)
+  for (int a = 0; a < c->d; ++a) {
     launch_setup_axis(c->c, c->n[a], c->L[a], c->lam[a], c->circ[a], c->tw64[a], c->tw32[a], c->stream);
+    if (p->precond == 1)
+      launch_setup_circ(c->c, c->n[a], c->L[a], c->lamC[a], c->chirp64[a], c->chirp32[a], c->bspec64[a],
+                        c->bspec32[a], c->stream);
+  }
   for (int h = 0; h < 2; ++h) {  // h = 1: the first step's mu_a / 2
     const double hf = h ? 0.5 : 1.0;
     launch_setup_lamfac(c->lam[0], c->lam[1], c->lam[2], c->n[0], c->n[1], c->n[2], hf * c->mu[0], hf * c->mu[1],
-                        hf * c->mu[2], p->omega, 1.0 / std::sqrt((double)c->L[c->d - 1]), c->lamfac64[h],
+                        hf * c->mu[2], p->omega, 1.0 / std::sqrt((double)c->L[c->d - 1]), 0, c->lamfac64[h],
                         c->lamfac32[h], N, c->stream);
+    if (p->precond == 1)
+      launch_setup_lamfac(c->lamC[0], c->lamC[1], c->lamC[2], c->n[0], c->n[1], c->n[2], hf * c->mu[0],
+                          hf * c->mu[1], hf * c->mu[2], p->omega, 1.0 / (double)N, 1, c->lamfacC64[h],
+                          c->lamfacC32[h], N, c->stream);
     for (int a = 0; a < c->d; ++a)
       launch_scale_circ(c->circ[a], c->L[a], hf * c->mu[a] / c->L[a], c->circ64s[h][a], c->circ32s[h][a],
                         c->stream);

@@ -256,7 +256,7 @@ __global__ void k_combine_dev(const double2* __restrict__ V, long long ldv, cons
                               double2* __restrict__ out, long long N) {
   __shared__ double y[kMaxM];
   const int k = gs->j;
-  if (threadIdx.x < k) y[threadIdx.x] = gs->y[threadIdx.x];
+  for (int t = threadIdx.x; t < k; t += blockDim.x) y[t] = gs->y[t];
   __syncthreads();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     double2 a = make_double2(0.0, 0.0);
@@ -305,7 +305,7 @@ __global__ void k_resid_update(const double2* __restrict__ V, long long ldv, con
   if (!gs->upd) return;  // uniform
   __shared__ double q[kMaxM + 1];
   const int k = k_in >= 0 ? k_in : gs->j;
-  if (threadIdx.x <= k) q[threadIdx.x] = gs->q[threadIdx.x];
+  for (int t = threadIdx.x; t <= k; t += blockDim.x) q[t] = gs->q[t];
   __syncthreads();
   const double cw = (q[k] == 0.0) ? 0.0 : q[k] * gs->inv_h;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
@@ -325,7 +325,7 @@ __global__ void k_combine_f32_add_dev(const float2* __restrict__ Z, long long ld
                                       double2* __restrict__ x, long long N) {
   __shared__ double y[kMaxM];
   const int k = gs->j;
-  if (threadIdx.x < k) y[threadIdx.x] = gs->y[threadIdx.x];
+  for (int t = threadIdx.x; t < k; t += blockDim.x) y[t] = gs->y[t];
   __syncthreads();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     double2 a = x[i];

@@ -10,7 +10,7 @@
 
 namespace rfnse {
 
-constexpr int kMaxM = 64;  // largest supported restart length
+constexpr int kMaxM = 256;  // largest supported restart length
 
 // Number of kernels this library has launched in the process (all contexts).
 extern std::atomic<long long> g_kernel_launches;
@@ -136,9 +136,13 @@ void launch_setup_coefficients(double* c, int nmax, double alpha, cudaStream_t s
 void launch_setup_axis(const double* c, int n, int L, double* lam, double* circ, double2* tw64, float2* tw32,
                        cudaStream_t s);
 // lamfac[g] = i dst_scale / (w + i sum_a mu_a lambda_a(k_a(g))) for every grid index g
+// circ = 1: lamfac[g] = dst_scale / (w + i Lambda) (the circulant comparator in the DFT basis)
 void launch_setup_lamfac(const double* lam0, const double* lam1, const double* lam2, int n0, int n1, int n2,
-                         double mu0, double mu1, double mu2, double omega, double dst_scale, double2* f64,
-                         float2* f32, long long N, cudaStream_t s);
+                         double mu0, double mu1, double mu2, double omega, double dst_scale, int circ,
+                         double2* f64, float2* f32, long long N, cudaStream_t s);
+// Strang-circulant comparator tables of one axis (setup.cu): eigenvalues, chirp, Bluestein spectrum
+void launch_setup_circ(const double* c, int n, int L, double* lamC, double2* chirp64, float2* chirp32,
+                       double2* bspec64, float2* bspec32, cudaStream_t s);
 // scaled circulant spectrum circ * scale in FP64 and FP32
 void launch_scale_circ(const double* circ, int L, double scale, double* c64, float* c32, cudaStream_t s);
 
@@ -178,6 +182,16 @@ struct rfnse_ctx {
   float2* lamfac32[2] = {nullptr, nullptr};
   double* circ64s[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};  // circ * mu_a hf / L
   float* circ32s[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  // Strang-circulant comparator (precond = 1): per axis the eigenvalues of Strang's circulant of T_0,
+  // the chirp exp(i pi j^2/n) and the Bluestein filter spectrum (1/L folded in); per point
+  // 1/(n_0 n_1 n_2 (w + i Lambda_C(k))) for [half]
+  double* lamC[3] = {nullptr, nullptr, nullptr};
+  double2* chirp64[3] = {nullptr, nullptr, nullptr};
+  float2* chirp32[3] = {nullptr, nullptr, nullptr};
+  double2* bspec64[3] = {nullptr, nullptr, nullptr};
+  float2* bspec32[3] = {nullptr, nullptr, nullptr};
+  double2* lamfacC64[2] = {nullptr, nullptr};
+  float2* lamfacC32[2] = {nullptr, nullptr};
   // mixed form: T u of each history vector, recovered from the final FP64 residual of the solve
   // that produced it (so the right-hand side two steps later needs no Toeplitz product)
   double2* Tu[3] = {nullptr, nullptr, nullptr};

@@ -163,7 +163,7 @@ __global__ void k_backsolve(GmresState* gs, int k) {
 __global__ void k_combine(const double2* __restrict__ V, long long ldv, const GmresState* gs, int k,
                           double2* __restrict__ out, long long N) {
   __shared__ double y[kMaxM];
-  if (threadIdx.x < k) y[threadIdx.x] = gs->y[threadIdx.x];
+  for (int t = threadIdx.x; t < k; t += blockDim.x) y[t] = gs->y[t];
   __syncthreads();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     double2 a = make_double2(0.0, 0.0);
@@ -180,7 +180,7 @@ __global__ void k_combine(const double2* __restrict__ V, long long ldv, const Gm
 __global__ void k_combine_f32_add(const float2* __restrict__ Z, long long ldz, const GmresState* gs, int k,
                                   double2* __restrict__ x, long long N) {
   __shared__ double y[kMaxM];
-  if (threadIdx.x < k) y[threadIdx.x] = gs->y[threadIdx.x];
+  for (int t = threadIdx.x; t < k; t += blockDim.x) y[t] = gs->y[t];
   __syncthreads();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     double2 a = x[i];

@@ -16,6 +16,12 @@
 //   F_TOEP_X   t = mu_a T_0^{(a)} z by circulant embedding (length-L FFT, multiply by the scaled
 //              circulant eigenvalues, inverse FFT) and acc = add + a z + b (t - D z)  (first axis)
 //   F_TOEP_ACC t = mu_a T_0^{(a)} z and acc = acc + b t                                  (other axes)
+//   F_CIRC     (with F_DST) the circulant comparator of Sec. 5: the transform is the unnormalised
+//              length-n DFT instead of S (forward, or inverse when inv_dft is set; with F_LAM forward,
+//              multiply, inverse), computed by Bluestein's chirp-z identity from one circular
+//              convolution of length L, i.e. two FFTs; no output scale (it is folded into lamfac).
+//   Without F_DST, F_DSCALE stores the loaded input itself (times dfac if given): the identity
+//   preconditioner of plain GMRES.
 //
 // With a = 1, b = i the Toeplitz passes give w = R z for the complex form R = I + i(T_d - D) of the
 // real block matrix R_d of eq. 'positiveBlockForm' (u = y + iz  <->  x = [z; y]).
@@ -39,6 +45,7 @@ enum : int {
   F_DSCALE = 8,
   F_TOEP_X = 16,
   F_TOEP_ACC = 32,
+  F_CIRC = 64,
 };
 
 struct PassParams {
@@ -71,6 +78,11 @@ struct PassParams {
   long long ldv;
   const int* skip;         // when set and nonzero, the launch does nothing
   int in_dyn_z;            // with gdyn: the input is Z[j] = zbase + j ldv (storage TIN)
+  // F_CIRC: chirp exp(i pi j^2/n) (length n) and Bluestein filter spectrum (length L, 1/L folded in),
+  // compute precision; inv_dft: the (first) transform is the inverse DFT
+  const void* chirp;
+  const void* bspec;
+  int inv_dft;
 };
 
 template <typename R> __device__ __forceinline__ cv<R> ld_c(const void* p, long long i);
@@ -79,6 +91,52 @@ template <> __device__ __forceinline__ double2 ld_c<double>(const void* p, long 
 }
 template <> __device__ __forceinline__ float2 ld_c<float>(const void* p, long long i) {
   return reinterpret_cast<const float2*>(p)[i];
+}
+
+// Unnormalised length-n DFT of every line of the tile by Bluestein's identity: element j of a line is
+// at position 1 + j (as everywhere in the passes); forward X_k = sum_j x_j exp(-2 pi i jk/n) =
+// conj(b_k) sum_j (x_j conj(b_j)) bt_{k-j}, inverse with b and conj(bt) (whose spectrum is conj(bspec):
+// bt is symmetric).  The circular convolution of length L >= 2n - 1 is exact for the needed range; its
+// input is zero from position n + 1 = L/2 on and only positions 1..n are read back, so the two FFTs
+// are the pruned ones of the Toeplitz products.  All threads of the block call this.
+template <typename R>
+__device__ __forceinline__ void bluestein_lines(cv<R>* buf, int Lp, int L, int log2L, int nt, const cv<R>* tws,
+                                                int n, int B, const void* chirp, const void* bspec, bool inv) {
+  using V = cv<R>;
+  const V zero = cvec<R>::make((R)0, (R)0);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const V* ch = reinterpret_cast<const V*>(chirp);
+  const V* bs = reinterpret_cast<const V*>(bspec);
+  for (int e = tid; e < B * L; e += nthr) {
+    const int l = e >> log2L, k = e & (L - 1);
+    V& v = buf[(size_t)l * Lp + fft_pad(k)];
+    if (k >= 1 && k <= n) {
+      V b = ch[k - 1];
+      if (!inv) b.y = -b.y;
+      v = cmul(v, b);
+    } else {
+      v = zero;
+    }
+  }
+  __syncthreads();
+  fft_lines(buf, Lp, L, log2L, nt, tws, false, /*zero_upper=*/true, false);
+  for (int e = tid; e < B * L; e += nthr) {
+    const int l = e >> log2L, k = e & (L - 1);
+    V s = bs[k];
+    if (inv) s.y = -s.y;
+    V& v = buf[(size_t)l * Lp + fft_pad(k)];
+    v = cmul(v, s);
+  }
+  __syncthreads();
+  fft_lines(buf, Lp, L, log2L, nt, tws, true, false, /*half_out=*/true);
+  for (int e = tid; e < B * n; e += nthr) {
+    const int l = e / n, j = e - l * n;
+    V b = ch[j];
+    if (!inv) b.y = -b.y;
+    V& v = buf[(size_t)l * Lp + fft_pad(1 + j)];
+    v = cmul(v, b);
+  }
+  __syncthreads();
 }
 
 template <typename R, typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS>
@@ -162,7 +220,7 @@ __global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
     }
     at(l, 1 + pos) = v;
     if (FLAGS & F_DST) {
-      at(l, L - 1 - pos) = cneg(v);               // odd extension y_{2(n+1)-j} = -x_j
+      if (!(FLAGS & F_CIRC)) at(l, L - 1 - pos) = cneg(v);   // odd extension y_{2(n+1)-j} = -x_j
     } else if (FLAGS & F_TOEP_X) {
       zsave[l * n + pos] = v;
     }
@@ -171,7 +229,7 @@ __global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
     at(l, 0) = zero;
     at(l, Nh) = zero;
   }
-  if (!(FLAGS & F_DST)) {                          // zero padding of the circulant embedding
+  if (!(FLAGS & F_DST) || (FLAGS & F_CIRC)) {      // zero padding of the circulant embedding
     for (int e = tid; e < B * (Nh - 1); e += nthr) {
       const int l = e / (Nh - 1);
       at(l, Nh + 1 + (e - l * (Nh - 1))) = zero;
@@ -181,8 +239,25 @@ __global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
 
   const R dsc = sizeof(R) == 4 ? (R)p.dst_scale_f : (R)p.dst_scale;
 
+  // ---- circulant comparator: DFTs by Bluestein ------------------------------------------------
+  if ((FLAGS & F_DST) && (FLAGS & F_CIRC)) {
+    bluestein_lines<R>(buf, Lp, L, p.log2L, p.nt, tws, n, B, p.chirp, p.bspec, (FLAGS & F_LAM) ? false : p.inv_dft != 0);
+    if (FLAGS & F_LAM) {
+      for (int e = tid; e < B * n; e += nthr) {
+        int l, pos;
+        map(e, l, pos);
+        bool valid;
+        const long long g = gidx(l, pos, valid);
+        const V f = valid ? ld_c<R>(p.lamfac, g) : zero;   // mode index = grid index on this axis
+        at(l, 1 + pos) = cmul(at(l, 1 + pos), f);
+      }
+      __syncthreads();
+      bluestein_lines<R>(buf, Lp, L, p.log2L, p.nt, tws, n, B, p.chirp, p.bspec, true);
+    }
+  }
+
   // ---- sine transforms ------------------------------------------------------------------------
-  if (FLAGS & F_DST) {
+  if ((FLAGS & F_DST) && !(FLAGS & F_CIRC)) {
     fft_lines(buf, Lp, L, p.log2L, p.nt, tws, false);
     if (FLAGS & F_LAM) {
       for (int e = tid; e < B * n; e += nthr) {
@@ -212,7 +287,7 @@ __global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
       map(e, l, pos);
       bool valid;
       const long long g = gidx(l, pos, valid);
-      if (valid) st_c(out + g, cmul_i(cscale(at(l, 1 + pos), dsc)));
+      if (valid) st_c(out + g, (FLAGS & F_CIRC) ? at(l, 1 + pos) : cmul_i(cscale(at(l, 1 + pos), dsc)));
     }
   }
   if (FLAGS & F_DSCALE) {
@@ -225,7 +300,9 @@ __global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
       const long long g = gidx(l, pos, valid);
       V z = zero;
       if (valid) {
-        z = cmul(cmul_i(cscale(at(l, 1 + pos), dsc)), ld_c<R>(p.dfac, g));
+        z = at(l, 1 + pos);                                   // identity preconditioner: the input
+        if ((FLAGS & F_DST) && !(FLAGS & F_CIRC)) z = cmul_i(cscale(z, dsc));
+        if (p.dfac) z = cmul(z, ld_c<R>(p.dfac, g));
         if (out) {
           if (p.z_add) st_c(out + g, cadd(to_c<R>(out[g]), z));
           else st_c(out + g, z);
@@ -303,15 +380,15 @@ template <typename R, typename TIN, typename TOUT, typename TACCI, typename TACC
 void pass_work(const PassParams& p, double& flops, double& bytes) {
   const double lines = (double)p.nlines, N = lines * p.n;
   int nfft = 0;
-  if (FLAGS & F_DST) ++nfft;
-  if (FLAGS & F_LAM) ++nfft;
+  if (FLAGS & F_DST) nfft += (FLAGS & F_CIRC) ? 2 : 1;
+  if (FLAGS & F_LAM) nfft += (FLAGS & F_CIRC) ? 2 : 1;
   if (FLAGS & (F_TOEP_X | F_TOEP_ACC)) nfft += 2;
   flops = lines * nfft * 5.0 * p.L * p.log2L;
   bytes = N * sizeof(TIN);
   if (FLAGS & F_INSCALE) bytes += N * sizeof(double2);
   if ((FLAGS & F_DST) && p.out) bytes += N * sizeof(TOUT) * (p.z_add ? 2 : 1);
   if (FLAGS & F_LAM) bytes += N * sizeof(cv<R>);
-  if (FLAGS & F_DSCALE) bytes += N * sizeof(cv<R>);
+  if ((FLAGS & F_DSCALE) && p.dfac) bytes += N * sizeof(cv<R>);
   if ((FLAGS & F_TOEP_X) && p.Dr) bytes += N * sizeof(R);
   if (FLAGS & (F_TOEP_X | F_TOEP_ACC)) bytes += N * sizeof(TACCO) + (p.acc_in ? N * sizeof(TACCI) : 0.0);
 }

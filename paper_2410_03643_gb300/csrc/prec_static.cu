@@ -79,6 +79,7 @@ extern "C" int rfnse_apply_prec_static(const rfnse_params* p, const void* v, voi
   rfnse_ctx c;
   c.p = *p;
   c.p.precision = 0;
+  c.p.precond = 0;  // the sine-transform preconditioner F~ only
   c.stream = (cudaStream_t)stream;
   c.d = p->d;
   c.N = 1;
@@ -125,7 +126,7 @@ extern "C" int rfnse_apply_prec_static(const rfnse_params* p, const void* v, voi
     launch_setup_axis(c.c, c.n[a], c.L[a], c.lam[a], c.circ[a], c.tw64[a], c.tw32[a], c.stream);
   const double hf = half ? 0.5 : 1.0;
   launch_setup_lamfac(c.lam[0], c.lam[1], c.lam[2], c.n[0], c.n[1], c.n[2], hf * c.mu[0], hf * c.mu[1],
-                      hf * c.mu[2], p->omega, 1.0 / std::sqrt((double)c.L[c.d - 1]), c.lamfac64[hidx],
+                      hf * c.mu[2], p->omega, 1.0 / std::sqrt((double)c.L[c.d - 1]), 0, c.lamfac64[hidx],
                       c.lamfac32[hidx], c.N, c.stream);
   if (cudaGetLastError() != cudaSuccess) return RFNSE_ECUDA;
   if (run_apply_prec(&c, (const double2*)v, (double2*)z, D, half ? 1 : 0, 0) != cudaSuccess) return RFNSE_ECUDA;

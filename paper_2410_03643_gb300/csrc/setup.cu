@@ -58,13 +58,61 @@ __global__ void k_axis_tables(const double* __restrict__ c, int n, int L, double
   tw32[k] = make_float2((float)cs, (float)-sn);
 }
 
+// Strang-circulant comparator (Sec. 5, F_C), one axis with n points (n odd) and L = 2(n+1):
+//   lamC[k] = c_0 + 2 sum_{m=1}^{(n-1)/2} c_m cos(2 pi m k/n), k < n: the eigenvalues of Strang's
+//     circulant of T_0 (first column c_0..c_{(n-1)/2}, c_{(n-1)/2}..c_1);
+//   chirp[j] = exp(i pi j^2/n), j < n (argument reduced mod 2n);
+//   bspec[k] = (1/L) sum_j bt_j exp(-2 pi i jk/L), the spectrum of the Bluestein filter
+//     bt_j = chirp[j] (0 <= j < n), bt_{L-j} = chirp[j] (0 < j < n), 0 otherwise, which is symmetric,
+//     so bspec[k] = (1/L)(chirp[0] + 2 sum_{m=1}^{n-1} chirp[m] cos(2 pi m k/L)).
+// With these a length-n DFT is X_k = conj(b_k) sum_j (x_j conj(b_j)) bt_{k-j} (jk = (j^2 + k^2 -
+// (k-j)^2)/2): one length-L circular convolution, i.e. two FFTs of length L.
+__device__ __forceinline__ double2 chirp_at(long long j, int n) {
+  const long long q = (j * j) % (2LL * n);
+  double sn, cs;
+  sincospi((double)q / (double)n, &sn, &cs);
+  return make_double2(cs, sn);
+}
+
+__global__ void k_circ_tables(const double* __restrict__ c, int n, int L, double* __restrict__ lamC,
+                              double2* __restrict__ chirp64, float2* __restrict__ chirp32,
+                              double2* __restrict__ bspec64, float2* __restrict__ bspec32) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= L) return;
+  if (k < n) {
+    double s = 0.0;
+    for (int m = (n - 1) / 2; m >= 1; --m) {
+      const long long mk = ((long long)m * k) % n;
+      s += c[m] * cospi(2.0 * (double)mk / (double)n);
+    }
+    lamC[k] = c[0] + 2.0 * s;
+    const double2 b = chirp_at(k, n);
+    chirp64[k] = b;
+    chirp32[k] = make_float2((float)b.x, (float)b.y);
+  }
+  double re = 0.0, im = 0.0;
+  for (int m = n - 1; m >= 1; --m) {
+    const double2 b = chirp_at(m, n);
+    const long long mk = ((long long)m * k) % L;
+    const double cw = cospi(2.0 * (double)mk / (double)L);
+    re += b.x * cw;
+    im += b.y * cw;
+  }
+  const double2 b0 = chirp_at(0, n);
+  const double2 v = make_double2((b0.x + 2.0 * re) / L, (b0.y + 2.0 * im) / L);
+  bspec64[k] = v;
+  bspec32[k] = make_float2((float)v.x, (float)v.y);
+}
+
 // Per-mode factor of the (omega I + tau(T_d)) sub-solve in the DST basis (eq. 'taupre', '2Dtau'):
 //   lamfac[g] = i dst_scale / (omega + i Lambda),  Lambda = sum_a mu_a lambda_a(k_a),
 // where (k_0, k_1, k_2) are the (0-based) mode indices of grid index g, x fastest.  i dst_scale is
 // the output scale of the DST-I computed from an FFT (folded in so the pass multiplies once).
+// circ = 1 (the circulant comparator, DFT basis): lamfac[g] = dst_scale / (omega + i Lambda), with
+// dst_scale = 1/(n_0 n_1 n_2), the scale of the unnormalised forward and inverse DFTs.
 __global__ void k_lamfac(const double* __restrict__ lam0, const double* __restrict__ lam1,
                          const double* __restrict__ lam2, int n0, int n1, int n2, double mu0, double mu1,
-                         double mu2, double omega, double dst_scale, double2* __restrict__ f64,
+                         double mu2, double omega, double dst_scale, int circ, double2* __restrict__ f64,
                          float2* __restrict__ f32, long long N) {
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
     long long r = g;
@@ -76,9 +124,10 @@ __global__ void k_lamfac(const double* __restrict__ lam0, const double* __restri
     double lam = mu0 * lam0[k0];
     if (lam1) lam += mu1 * lam1[k1];
     if (lam2) lam += mu2 * lam2[k2];
-    // i s/(w + i lam) = s (lam + i w)/(w^2 + lam^2)
+    // i s/(w + i lam) = s (lam + i w)/(w^2 + lam^2);  s/(w + i lam) = s (w - i lam)/(w^2 + lam^2)
     const double den = omega * omega + lam * lam;
-    const double2 f = make_double2(dst_scale * lam / den, dst_scale * omega / den);
+    const double2 f = circ ? make_double2(dst_scale * omega / den, -dst_scale * lam / den)
+                           : make_double2(dst_scale * lam / den, dst_scale * omega / den);
     f64[g] = f;
     f32[g] = make_float2((float)f.x, (float)f.y);
   }
@@ -94,13 +143,19 @@ __global__ void k_scale_circ(const double* __restrict__ circ, int L, double scal
 }
 
 void launch_setup_lamfac(const double* lam0, const double* lam1, const double* lam2, int n0, int n1, int n2,
-                         double mu0, double mu1, double mu2, double omega, double dst_scale, double2* f64,
-                         float2* f32, long long N, cudaStream_t s) {
+                         double mu0, double mu1, double mu2, double omega, double dst_scale, int circ,
+                         double2* f64, float2* f32, long long N, cudaStream_t s) {
   long long blocks = (N + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
   count_launch();
-  k_lamfac<<<(unsigned)blocks, 256, 0, s>>>(lam0, lam1, lam2, n0, n1, n2, mu0, mu1, mu2, omega, dst_scale, f64,
-                                           f32, N);
+  k_lamfac<<<(unsigned)blocks, 256, 0, s>>>(lam0, lam1, lam2, n0, n1, n2, mu0, mu1, mu2, omega, dst_scale, circ,
+                                           f64, f32, N);
+}
+
+void launch_setup_circ(const double* c, int n, int L, double* lamC, double2* chirp64, float2* chirp32,
+                       double2* bspec64, float2* bspec32, cudaStream_t s) {
+  count_launch();
+  k_circ_tables<<<(L + 127) / 128, 128, 0, s>>>(c, n, L, lamC, chirp64, chirp32, bspec64, bspec32);
 }
 
 void launch_scale_circ(const double* circ, int L, double scale, double* c64, float* c32, cudaStream_t s) {

@@ -47,6 +47,7 @@ class Params(ctypes.Structure):
         ("inner_tol", ctypes.c_double),
         ("max_outer", ctypes.c_int),
         ("device_loop", ctypes.c_int),
+        ("precond", ctypes.c_int),
     ]
 
 
@@ -150,6 +151,7 @@ def make_params(problem, precision: int = 0, inner_tol: float = 1e-6, max_outer:
     p.inner_tol = inner_tol
     p.max_outer = max_outer
     p.device_loop = device_loop
+    p.precond = getattr(problem, "precond", 0)
     return p
 
 

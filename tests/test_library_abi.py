@@ -56,6 +56,7 @@ def test_params_struct_matches_defaults(libpath):
     assert p.d == 1 and p.restart == 20 and p.max_it == 2000 and p.omega == 1.0
     assert p.tol == 1e-10 and p.first_step == 1 and p.inner_tol == 1e-6 and p.max_outer == 30
     assert p.device_loop == 1
+    assert p.precond == 0
 
 
 def test_create_rejects_invalid_params_without_gpu_work(libpath):
@@ -63,7 +64,8 @@ def test_create_rejects_invalid_params_without_gpu_work(libpath):
     lib = rfnse.load_library()
     bad = []
     for field, value in (("d", 0), ("d", 4), ("alpha", 1.0), ("alpha", 2.5), ("dt", 0.0), ("restart", 0),
-                         ("restart", 65), ("precision", 2), ("omega", -1.0), ("tol", 0.0)):
+                         ("restart", 257), ("precision", 2), ("omega", -1.0), ("tol", 0.0), ("precond", 3),
+                         ("precond", -1)):
         p = rfnse.Params()
         lib.rfnse_default_params(ctypes.byref(p))
         setattr(p, field, value)
