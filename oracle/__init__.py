@@ -24,6 +24,8 @@ Everything here follows the paper's own formulation, in its notation:
                    Sec. 2.2 eq. 'discretizedRFSE2D'), its first step, and the discrete mass/energy.
 * ``circulant`` -- the comparators of Sec. 5: Strang's circulant TBAN preconditioner F_C (C-GMRES)
                    and no preconditioner (GMRES).
+* ``tban``      -- the TBAN iteration, Method 3.1 (Sec. 3), as printed (dense half-step solves) and in
+                   the stationary form x += P^{-1}(f - R x) with the practical preconditioners.
 * ``adjoint``   -- the reverse-mode gradient of that discrete scheme with respect to u^0 and rho
                    (derived from the scheme; the paper has no adjoint), one conjugate solve per step.
 
@@ -32,4 +34,4 @@ vectors, so that the complex-arithmetic CUDA path and this oracle reach the same
 different routes.  Transforms and Toeplitz products are dense matrix products (the plain
 definitions); no FFT is used anywhere in the oracle.
 """
-from . import fcd, operators, tau, precond, circulant, gmres, scheme, adjoint  # noqa: F401
+from . import fcd, operators, tau, precond, circulant, gmres, scheme, tban, adjoint  # noqa: F401
