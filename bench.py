@@ -8,12 +8,13 @@ FP64 Arnoldi/Givens and FP64 outer residual); the plain FP64 form is timed the s
 beside it, with the difference between the two trajectories.  DOF = complex grid unknowns.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload 2d|3d|1d|batched|adjoint|comparators]
+                  [--workload 2d|3d|1d|batched|adjoint|comparators|omega]
 
 Other workloads: 3d (255^3, mixed), 1d (n = 1023), batched (64 independent 2-D instances with grids
 drawn from {127, 255, 511}^2: one step = one graph launch advancing all of them), adjoint (255^2,
 20 steps, FP64: one step = a taped forward run plus its reverse pass, dL/du0 and dL/drho),
-comparators (255^2: the same run with the sine-transform preconditioner, Strang's circulant and none).
+comparators (255^2: the same run with the sine-transform preconditioner, Strang's circulant and none),
+omega (Fig. 1: tau-GMRES iterations versus the TBAN parameter w for five alpha, 1-D n = 2047).
 
 Multi-GPU (torchrun): every rank advances its own copy of the three instances (independent problems,
 no collective on the data path; weak scaling); value = all ranks' DOF x steps / max rank time.
@@ -66,7 +67,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="2d", choices=["2d", "3d", "1d", "batched", "adjoint", "comparators"])
+    ap.add_argument("--workload", default="2d", choices=["2d", "3d", "1d", "batched", "adjoint", "comparators", "omega"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
@@ -685,6 +686,52 @@ def run_comparators(args):
         print(json.dumps(out), flush=True)
 
 
+def run_omega(args):
+    """Fig. 1: tau-GMRES iterations at the 2nd time level versus the TBAN parameter w in (0, 4] for
+    alpha = 1.1:0.2:1.9 (1-D, [-20,20], rho = 2, sech(x)e^{2ix}, n = 2047, dt = 0.05, tol 1e-8, no
+    restart); the line's value is the solve throughput over the whole sweep."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    from paper_2410_03643_gb300 import build, rfnse
+    build.build_library()
+    main = torch.cuda.current_stream()
+    omegas = [round(0.1 * k, 1) for k in range(1, 41)]
+    curves, best, total_ms, nsolve = {}, {}, 0.0, 0
+    n = 2047
+    for alpha in (1.1, 1.3, 1.5, 1.7, 1.9):
+        its = []
+        for w in omegas:
+            p = W.Problem(d=1, n=(n,), lo=(-20.0,), hi=(20.0,), alpha=alpha, rho=2.0, dt=0.05, tol=1e-8, omega=w,
+                          restart=256)
+            s = rfnse.Solver(p, precision=0, stream=main)
+            u0 = torch.from_numpy(W.u0_sech_1d(p, 2.0)).to(dev)
+            s.set_state(u0)
+            s.run(1)
+            _, u1, _ = s.get_state()
+            D = (p.rho * p.dt) * torch.abs(u1) ** 2
+            b = -s.apply_A(u0, D) + 2j * u0
+            s.solve(D, b)                                    # warm: graph capture
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(main)
+            _, it, _ = s.solve(D, b)
+            e1.record(main)
+            torch.cuda.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            nsolve += 1
+            its.append(it)
+            s.close()
+        curves[str(alpha)] = its
+        best[str(alpha)] = omegas[int(np.argmin(its))]
+    out = {"metric": METRIC, "value": n * nsolve / (total_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": nsolve,
+           "warmup": 1, "ms_per_step": total_ms / nsolve, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (the 1-D test of Sec. 5.1)",
+           "config": {"workload": "omega_sweep_1d_n2047_rho2_dt0.05_tol1e-8", "what": "one step = one solve at "
+                      "the 2nd time level; w = 0.1:0.1:4.0 for each alpha"},
+           "omega": omegas, "iterations": curves, "best_omega": best}
+    print(json.dumps(out), flush=True)
+
+
 def alu_probe():
     import torch
     from paper_2410_03643_gb300 import build, rfnse
@@ -709,6 +756,8 @@ def main():
         run_adjoint(args)
     elif args.workload == "comparators":
         run_comparators(args)
+    elif args.workload == "omega":
+        run_omega(args)
     else:
         run_ours(args)
 

@@ -205,6 +205,16 @@ int rfnse_toeplitz(rfnse_ctx* ctx, int axis, const void* in, void* out, int half
 int rfnse_solve(rfnse_ctx* ctx, const double* D, const void* b, void* u, int half, int* iters,
                 double* relres);
 
+/* Solve (D - T + iI) u = b like rfnse_solve, but by the TBAN iteration (Sec. 3, Method 3.1) in its
+   stationary form F x^{k+1} = G x^k + f, i.e. x^{k+1} = x^k + F^{-1}(f - R x^k) from x^0 = 0, with the
+   context's preconditioner as F: the sine-transform F~ (precond = 0; Method 3.1 with tau(T_d) in
+   place of T_d inside F), the circulant F_C (1), or none (2, Richardson).  FP64 whatever the context's
+   precision.  Stops when the relative residual < tol or after max_it iterations (*iters receives the
+   count).  Arguments as rfnse_solve.  Errors: EINVAL, ECUDA, ENOCONV (u holds the last iterate),
+   ENUMERIC. */
+int rfnse_tban_solve(rfnse_ctx* ctx, const double* D, const void* b, void* u, int half, int* iters,
+                     double* relres);
+
 /* Copy the FCD coefficients c_0..c_{nmax-1} (nmax = largest n[a]) and the tau eigenvalues of T_0
    (not scaled by mu_a) of every axis, axis after axis (sum of n[a] values), to host memory.
    Either pointer may be NULL. */

@@ -383,6 +383,18 @@ int rfnse_solve(rfnse_ctx* c, const double* D, const void* b, void* u, int half,
   return st;
 }
 
+int rfnse_tban_solve(rfnse_ctx* c, const double* D, const void* b, void* u, int half, int* iters, double* relres) {
+  if (!c || !D || !b || !u || b == u) return RFNSE_EINVAL;
+  launch_neg_i((const double2*)b, c->f, c->N, c->stream);  // f = -i b  (Sec. 3: f = [-p; q])
+  int it = 0;
+  double rr = 0.0;
+  const rfnse_status st = tban_solve(c, D, c->f, (double2*)u, half ? 1 : 0, &it, &rr);
+  RFNSE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (iters) *iters = it;
+  if (relres) *relres = rr;
+  return st;
+}
+
 int rfnse_get_coefficients(rfnse_ctx* c, double* cc, double* lam) {
   if (!c) return RFNSE_EINVAL;
   int nmax = 0;

@@ -470,6 +470,47 @@ rfnse_status solve_block(rfnse_ctx* c, const double* D, const double2* f, double
 }
 
 // ---------------------------------------------------------------------------------------------
+// The TBAN iteration (Sec. 3, Method 3.1) in its stationary form F x^{k+1} = G x^k + f, i.e.
+// x^{k+1} = x^k + P^{-1}(f - R x^k), from x^0 = 0, with the context's preconditioner P as F (the
+// sine-transform F~: tau(T_d) in place of T_d; or the circulant F_C; or none, which is Richardson).
+// FP64 throughout; stops when ||f - R x|| / ||f|| < tol or after max_it iterations.
+rfnse_status tban_solve(rfnse_ctx* c, const double* D, const double2* f, double2* x, int half, int* iters,
+                        double* relres) {
+  const long long N = c->N;
+  GmresPeek pk;
+  *iters = 0;
+  *relres = 0.0;
+  RFNSE_CUDA_TRY(c, prepare_D(c, D));
+  launch_zero(x, N, c->stream);
+  launch_norm(f, c->gs, N, c->red_blocks, c->partials, c->counter, c->stream);
+  rfnse_status st = peek(c, &pk);
+  if (st) return st;
+  const double fnorm = pk.beta;
+  if (!std::isfinite(fnorm)) { c->err = "non-finite right-hand side"; return RFNSE_ENUMERIC; }
+  if (fnorm == 0.0) return RFNSE_OK;
+  const double2* r = f;
+  double rel = 1.0;
+  int k = 0;
+  while (k < c->p.max_it) {
+    RFNSE_CUDA_TRY(c, (run_precon<double, double2, double2, double2, double2, false, false>(
+                          c, r, nullptr, nullptr, x, 1, D, nullptr, nullptr, nullptr, kOne, kI, half, c->t1, c->t2)));
+    RFNSE_CUDA_TRY(c, run_matvec_fp64(c, x, D, c->r, f, kMinusOne, kMinusI, half, nullptr));
+    launch_norm(c->r, c->gs, N, c->red_blocks, c->partials, c->counter, c->stream);
+    if ((st = peek(c, &pk))) return st;
+    r = c->r;
+    ++k;
+    rel = pk.beta / fnorm;
+    if (!std::isfinite(rel)) { c->err = "non-finite residual"; return RFNSE_ENUMERIC; }
+    if (rel < c->p.tol) break;
+  }
+  *iters = k;
+  *relres = rel;
+  if (rel < c->p.tol) return RFNSE_OK;
+  c->err = "the TBAN iteration reached max_it";
+  return RFNSE_ENOCONV;
+}
+
+// ---------------------------------------------------------------------------------------------
 // Time steps (paper Sec. 2.1/2.2): (D - T + iI) u^{n+1} = (T - D + iI) u^{n-1}, solved in the
 // block form R x = f with f = -i b = u^{n-1} - i (T - D) u^{n-1}.
 //

@@ -13,6 +13,8 @@ cudaError_t run_apply_A(rfnse_ctx* c, const double2* u, double2* out, const doub
 rfnse_status solve_block(rfnse_ctx* c, const double* D, const double2* f, double2* x, int half, int* iters,
                          double* relres);
 rfnse_status time_step(rfnse_ctx* c, int* iters, double* relres);
+rfnse_status tban_solve(rfnse_ctx* c, const double* D, const double2* f, double2* x, int half, int* iters,
+                        double* relres);
 cudaError_t prepare_D(rfnse_ctx* c, const double* D);
 cudaError_t capture_solve(rfnse_ctx* c, int mixed, int half, cudaGraph_t g, cudaStream_t s);
 

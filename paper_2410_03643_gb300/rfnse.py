@@ -56,7 +56,7 @@ EXPORTED = ("rfnse_default_params", "rfnse_create", "rfnse_destroy", "rfnse_last
             "rfnse_dst", "rfnse_toeplitz", "rfnse_solve", "rfnse_get_coefficients", "rfnse_launch_count",
             "rfnse_profile", "rfnse_profile_read", "rfnse_probe_fma", "rfnse_batch_create",
             "rfnse_batch_destroy", "rfnse_batch_last_error", "rfnse_batch_context", "rfnse_batch_run",
-            "rfnse_tape_forward", "rfnse_tape_backward", "rfnse_adjoint_solve")
+            "rfnse_tape_forward", "rfnse_tape_backward", "rfnse_adjoint_solve", "rfnse_tban_solve")
 
 K_INSCALE, K_DST, K_LAM, K_DSCALE, K_TOEP_X, K_TOEP_ACC, K_FP32 = 1, 2, 4, 8, 16, 32, 256
 
@@ -125,6 +125,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.rfnse_tape_backward.restype = ip
     lib.rfnse_adjoint_solve.argtypes = [vp, vp, vp, vp, ip, ctypes.POINTER(ctypes.c_int), dp]
     lib.rfnse_adjoint_solve.restype = ip
+    lib.rfnse_tban_solve.argtypes = [vp, vp, vp, vp, ip, ctypes.POINTER(ctypes.c_int), dp]
+    lib.rfnse_tban_solve.restype = ip
     if path == _build.library_path():
         _lib = lib
     return lib
@@ -286,6 +288,18 @@ class Solver:
         rr = ctypes.c_double()
         self._check(self.lib.rfnse_solve(self.h, _ptr(D), _ptr(b), _ptr(u), int(half), ctypes.byref(it),
                                          ctypes.byref(rr)))
+        return u, it.value, rr.value
+
+    def tban_solve(self, D, b, half: bool = False, allow_noconv: bool = False):
+        """u with (D - T + iI) u = b by the stationary TBAN iteration; returns (u, iters, relres)."""
+        import torch
+        u = torch.empty_like(b)
+        it = ctypes.c_int()
+        rr = ctypes.c_double()
+        st = self.lib.rfnse_tban_solve(self.h, _ptr(D), _ptr(b), _ptr(u), int(half), ctypes.byref(it),
+                                       ctypes.byref(rr))
+        if not (allow_noconv and st == RFNSE_ENOCONV):
+            self._check(st)
         return u, it.value, rr.value
 
     def adjoint_solve(self, D, g, half: bool = False):
