@@ -34,6 +34,7 @@
 #include <cstdint>
 #include "cplx.cuh"
 #include "fft_line.cuh"
+#include "fft_fixed.cuh"
 #include "internal.cuh"
 
 namespace rfnse {
@@ -93,13 +94,25 @@ template <> __device__ __forceinline__ float2 ld_c<float>(const void* p, long lo
   return reinterpret_cast<const float2*>(p)[i];
 }
 
+// FP32 passes whose FFT length passes fixed_fft_length (fft_fixed.cuh) are compiled with the length
+// fixed (radix-8 register butterflies, twiddles read from the global per-stage table through L1); all
+// other passes use the runtime-length radix-4 FFT of fft_line.cuh with the table in shared memory.
+template <int LOG2L, bool INV, bool ZU, bool HO, typename V>
+__device__ __forceinline__ void fft_any(V* buf, int Lp, int L, int log2L, int nt, int B, const V* tw) {
+  if constexpr (LOG2L > 0) {
+    fft_lines_fixed<LOG2L, kFixedLogR, INV, ZU, HO>(buf, Lp, B, tw);
+  } else {
+    fft_lines(buf, Lp, L, log2L, nt, tw, INV, ZU, HO);
+  }
+}
+
 // Unnormalised length-n DFT of every line of the tile by Bluestein's identity: element j of a line is
 // at position 1 + j (as everywhere in the passes); forward X_k = sum_j x_j exp(-2 pi i jk/n) =
 // conj(b_k) sum_j (x_j conj(b_j)) bt_{k-j}, inverse with b and conj(bt) (whose spectrum is conj(bspec):
 // bt is symmetric).  The circular convolution of length L >= 2n - 1 is exact for the needed range; its
 // input is zero from position n + 1 = L/2 on and only positions 1..n are read back, so the two FFTs
 // are the pruned ones of the Toeplitz products.  All threads of the block call this.
-template <typename R>
+template <typename R, int LOG2L>
 __device__ __forceinline__ void bluestein_lines(cv<R>* buf, int Lp, int L, int log2L, int nt, const cv<R>* tws,
                                                 int n, int B, const void* chirp, const void* bspec, bool inv) {
   using V = cv<R>;
@@ -119,7 +132,7 @@ __device__ __forceinline__ void bluestein_lines(cv<R>* buf, int Lp, int L, int l
     }
   }
   __syncthreads();
-  fft_lines(buf, Lp, L, log2L, nt, tws, false, /*zero_upper=*/true, false);
+  fft_any<LOG2L, false, true, false>(buf, Lp, L, log2L, nt, B, tws);   // zero upper half in
   for (int e = tid; e < B * L; e += nthr) {
     const int l = e >> log2L, k = e & (L - 1);
     V s = bs[k];
@@ -128,7 +141,7 @@ __device__ __forceinline__ void bluestein_lines(cv<R>* buf, int Lp, int L, int l
     v = cmul(v, s);
   }
   __syncthreads();
-  fft_lines(buf, Lp, L, log2L, nt, tws, true, false, /*half_out=*/true);
+  fft_any<LOG2L, true, false, true>(buf, Lp, L, log2L, nt, B, tws);    // lower half out
   for (int e = tid; e < B * n; e += nthr) {
     const int l = e / n, j = e - l * n;
     V b = ch[j];
@@ -139,21 +152,25 @@ __device__ __forceinline__ void bluestein_lines(cv<R>* buf, int Lp, int L, int l
   __syncthreads();
 }
 
-template <typename R, typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS>
-__global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
+constexpr int kPassMaxThreads = 512;  // the line-pass kernels' launch bound
+
+template <typename R, typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS, int LOG2L>
+__global__ void __launch_bounds__(kPassMaxThreads) k_line_pass(const PassParams p) {
   using V = cv<R>;
   if (p.skip && *p.skip) return;  // uniform: the whole launch is a no-op
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = p.L, n = p.n, Nh = L >> 1, B = p.B;
   const int Lp = fft_line_stride(L);
   V* buf = reinterpret_cast<V*>(smem_raw);
-  V* tws = buf + (size_t)B * Lp;
-  V* zsave = tws + L;
+  V* zsave = buf + (size_t)B * Lp + (LOG2L > 0 ? 0 : L);
+  // twiddles: staged in shared memory for the runtime-length FFT, read from the table otherwise
+  const V* tws = (LOG2L > 0) ? reinterpret_cast<const V*>(p.tw) : buf + (size_t)B * Lp;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const bool xax = (p.stride == 1);
   const V zero = cvec<R>::make((R)0, (R)0);
 
-  for (int i = tid; i < L; i += nthr) tws[i] = ld_c<R>(p.tw, i);
+  if (LOG2L == 0)
+    for (int i = tid; i < L; i += nthr) (buf + (size_t)B * Lp)[i] = ld_c<R>(p.tw, i);
 
   long long line0 = 0, hi = 0, lo0 = 0;
   if (xax) {
@@ -241,7 +258,8 @@ __global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
 
   // ---- circulant comparator: DFTs by Bluestein ------------------------------------------------
   if ((FLAGS & F_DST) && (FLAGS & F_CIRC)) {
-    bluestein_lines<R>(buf, Lp, L, p.log2L, p.nt, tws, n, B, p.chirp, p.bspec, (FLAGS & F_LAM) ? false : p.inv_dft != 0);
+    bluestein_lines<R, LOG2L>(buf, Lp, L, p.log2L, p.nt, tws, n, B, p.chirp, p.bspec,
+                              (FLAGS & F_LAM) ? false : p.inv_dft != 0);
     if (FLAGS & F_LAM) {
       for (int e = tid; e < B * n; e += nthr) {
         int l, pos;
@@ -252,13 +270,13 @@ __global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
         at(l, 1 + pos) = cmul(at(l, 1 + pos), f);
       }
       __syncthreads();
-      bluestein_lines<R>(buf, Lp, L, p.log2L, p.nt, tws, n, B, p.chirp, p.bspec, true);
+      bluestein_lines<R, LOG2L>(buf, Lp, L, p.log2L, p.nt, tws, n, B, p.chirp, p.bspec, true);
     }
   }
 
   // ---- sine transforms ------------------------------------------------------------------------
   if ((FLAGS & F_DST) && !(FLAGS & F_CIRC)) {
-    fft_lines(buf, Lp, L, p.log2L, p.nt, tws, false);
+    fft_any<LOG2L, false, false, false>(buf, Lp, L, p.log2L, p.nt, B, tws);
     if (FLAGS & F_LAM) {
       for (int e = tid; e < B * n; e += nthr) {
         int l, pos;
@@ -275,7 +293,7 @@ __global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
         at(l, Nh) = zero;
       }
       __syncthreads();
-      fft_lines(buf, Lp, L, p.log2L, p.nt, tws, false);
+      fft_any<LOG2L, false, false, false>(buf, Lp, L, p.log2L, p.nt, B, tws);
     }
   }
 
@@ -329,7 +347,7 @@ __global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
   // ---- Toeplitz product by circulant embedding ------------------------------------------------
   if (FLAGS & (F_TOEP_X | F_TOEP_ACC)) {
     // the embedded vector is zero from position L/2 on, and only positions 1..n < L/2 are read back
-    fft_lines(buf, Lp, L, p.log2L, p.nt, tws, false, /*zero_upper=*/true, false);
+    fft_any<LOG2L, false, true, false>(buf, Lp, L, p.log2L, p.nt, B, tws);   // zero upper half in
     const R* circ = reinterpret_cast<const R*>(p.circ);
     for (int e = tid; e < B * L; e += nthr) {
       const int l = e >> p.log2L;
@@ -337,7 +355,7 @@ __global__ void __launch_bounds__(512) k_line_pass(const PassParams p) {
       at(l, k) = cscale(at(l, k), circ[k]);
     }
     __syncthreads();
-    fft_lines(buf, Lp, L, p.log2L, p.nt, tws, true, false, /*half_out=*/true);
+    fft_any<LOG2L, true, false, true>(buf, Lp, L, p.log2L, p.nt, B, tws);    // lower half out
     const V ca = sizeof(R) == 4 ? cvec<R>::make((R)p.ca_f.x, (R)p.ca_f.y) : cvec<R>::make((R)p.ca.x, (R)p.ca.y);
     const V cb = sizeof(R) == 4 ? cvec<R>::make((R)p.cb_f.x, (R)p.cb_f.y) : cvec<R>::make((R)p.cb.x, (R)p.cb.y);
     const TACCI* accin = reinterpret_cast<const TACCI*>(p.acc_in);
@@ -374,6 +392,50 @@ inline void pass_geometry(int L, bool xax, long long lines_avail, int& nt, int& 
   while (B > 1 && B > lines_avail) B >>= 1;  // keep B a power of two
 }
 
+// The fixed-length FFT: L / 2^kFixedLogR threads per line; blocks of up to 128 threads along x and 256
+// along a strided axis (B lines adjacent in x, so B >= 2 keeps 16-byte runs per row), with fewer lines
+// per block while that leaves fewer than two blocks per SM (152 SMs).  Measured on the 2-D 511^2 and
+// 3-D 255^3 workloads against 1..4 lines per block on each axis.
+inline void pass_geometry_fixed(int L, bool xax, long long lines_avail, long long nlines, int& nt, int& B) {
+  nt = L >> kFixedLogR;
+  B = (xax ? 128 : 256) / nt;
+  if (B < 1) B = 1;
+  while (B > 1 && B * nt > kPassMaxThreads) B >>= 1;
+  while (B > 1 && B > lines_avail) B >>= 1;
+  auto blocks = [&](int b) -> long long {
+    return xax ? (nlines + b - 1) / b : ((lines_avail + b - 1) / b) * (nlines / lines_avail);
+  };
+  const int bmin = xax ? 1 : 2;
+  while (B > bmin && blocks(B) < 2 * 152) B >>= 1;
+}
+
+template <typename R, typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS>
+struct PassKernels {
+  using Fn = void (*)(const PassParams);
+  static Fn get(int log2L) {
+    if constexpr (sizeof(R) == 4) {
+      switch (log2L) {
+        case 8: return k_line_pass<R, TIN, TOUT, TACCI, TACCO, FLAGS, 8>;
+        case 9: return k_line_pass<R, TIN, TOUT, TACCI, TACCO, FLAGS, 9>;
+        case 10: return k_line_pass<R, TIN, TOUT, TACCI, TACCO, FLAGS, 10>;
+        case 11: return k_line_pass<R, TIN, TOUT, TACCI, TACCO, FLAGS, 11>;
+        default: break;
+      }
+    }
+    return k_line_pass<R, TIN, TOUT, TACCI, TACCO, FLAGS, 0>;
+  }
+  // dynamic shared memory above 48 KB for every variant, once per process (thread-safe static init)
+  static cudaError_t allow_smem() {
+    cudaError_t e = cudaSuccess;
+    for (int lg = 0; lg <= 12; ++lg) {
+      if (lg != 0 && !(sizeof(R) == 4 && fixed_fft_length(lg))) continue;
+      const cudaError_t r = cudaFuncSetAttribute(get(lg), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (e == cudaSuccess) e = r;
+    }
+    return e;
+  }
+};
+
 // Algorithmic work of one launch: 5 L log2 L flops per complex FFT of length L per line, and
 // bytes with every operand read once and every result written once.
 template <typename R, typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS>
@@ -397,7 +459,9 @@ template <typename R, typename TIN, typename TOUT, typename TACCI, typename TACC
 cudaError_t launch_pass(rfnse_ctx* c, PassParams p, cudaStream_t s) {
   using V = cv<R>;
   const bool xax = (p.stride == 1);
-  pass_geometry(p.L, xax, xax ? p.nlines : p.stride, p.nt, p.B);
+  const bool fixed = sizeof(R) == 4 && fixed_fft_length(p.log2L);
+  if (fixed) pass_geometry_fixed(p.L, xax, xax ? p.nlines : p.stride, p.nlines, p.nt, p.B);
+  else pass_geometry(p.L, xax, xax ? p.nlines : p.stride, p.nt, p.B);
   p.dst_scale_f = (float)p.dst_scale;
   p.ca_f = make_float2((float)p.ca.x, (float)p.ca.y);
   p.cb_f = make_float2((float)p.cb.x, (float)p.cb.y);
@@ -412,13 +476,16 @@ cudaError_t launch_pass(rfnse_ctx* c, PassParams p, cudaStream_t s) {
     const long long nhi = p.nlines / p.stride;
     grid = p.tiles_inner * nhi;
   }
-  size_t smem = ((size_t)p.B * fft_line_stride(p.L) + p.L) * sizeof(V);
+  size_t smem = ((size_t)p.B * fft_line_stride(p.L) + (fixed ? 0 : p.L)) * sizeof(V);
   if (FLAGS & F_TOEP_X) smem += (size_t)p.B * p.n * sizeof(V);
-  auto kern = k_line_pass<R, TIN, TOUT, TACCI, TACCO, FLAGS>;
-  static const cudaError_t attr_err =
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  using K = PassKernels<R, TIN, TOUT, TACCI, TACCO, FLAGS>;
+  const auto kern = K::get(fixed ? p.log2L : 0);
+  static const cudaError_t attr_err = K::allow_smem();
   if (attr_err != cudaSuccess) return attr_err;
   if (grid <= 0) return cudaSuccess;
+  // a block above the launch bound would fail to launch (inside a stream capture that invalidates the
+  // whole capture): refuse it here, before any launch
+  if (p.B * p.nt > kPassMaxThreads || p.B * p.nt < 1) return cudaErrorInvalidConfiguration;
   const int kind = FLAGS | (sizeof(R) == 4 ? 256 : 0);
   const bool prof = c->prof_kind != 0 && ((c->prof_kind | F_INSCALE) == (kind | F_INSCALE));
   cudaEvent_t e0 = nullptr, e1 = nullptr;

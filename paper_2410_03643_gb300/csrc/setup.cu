@@ -1,6 +1,7 @@
 // Set-up kernels, run once per context: FCD coefficients (paper Sec. 2.1), tau eigenvalues
 // (Sec. 4), circulant eigenvalues of the Toeplitz embedding and FFT twiddles.
 #include "internal.cuh"
+#include "fft_fixed.cuh"
 
 namespace rfnse {
 
@@ -25,7 +26,8 @@ __global__ void k_coefficients(double* c, int nmax, double alpha) {
 //     leading n x n block;
 //   lam[k-1] = circ[k], k = 1..n: the eigenvalues of tau(T_0) = T_0 - HC(T_0) (eq. 'taudefine',
 //     'taudiagonal'), i.e. c_0 + 2 sum_m c_m cos(pi m k/(n+1)).
-//   tw: the per-stage twiddle table of a length-L FFT (layout in fft_line.cuh), FP64 and FP32.
+//   tw: the per-stage twiddle table of a length-L FFT, FP64 in the layout of fft_line.cuh, FP32 in
+//     that of fft_fixed.cuh for the lengths the FP32 passes compile with a fixed FFT.
 __global__ void k_axis_tables(const double* __restrict__ c, int n, int L, double* __restrict__ lam,
                               double* __restrict__ circ, double2* __restrict__ tw64, float2* __restrict__ tw32) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -55,7 +57,15 @@ __global__ void k_axis_tables(const double* __restrict__ c, int n, int L, double
     sincospi((double)(r * kk) / (double)(2 * Ns), &sn, &cs);
   }
   tw64[k] = make_double2(cs, -sn);
-  tw32[k] = make_float2((float)cs, (float)-sn);
+  if (fixed_fft_length(log2L)) {  // the FP32 passes of these lengths use the fixed-length FFT's layout
+    int R, ns, r, kk;
+    fixed_twiddle_entry(log2L, kFixedLogR, k, R, ns, r, kk);
+    double s2 = 0.0, c2 = 1.0;
+    if (R > 1) sincospi(2.0 * (double)(r * kk) / (double)(R * ns), &s2, &c2);
+    tw32[k] = make_float2((float)c2, (float)-s2);
+  } else {
+    tw32[k] = make_float2((float)cs, (float)-sn);
+  }
 }
 
 // Strang-circulant comparator (Sec. 5, F_C), one axis with n points (n odd) and L = 2(n+1):
