@@ -58,7 +58,9 @@ def measured_hbm_gbs():
 
 
 # DRAM read+write per launch of the FP32 fused DST-x + (wI+D) + Toeplitz-x pass (ncu, 2-D 511^2)
-TRAFFIC_FP32_FUSED_X = {"2d": 5288192 + 0}
+TRAFFIC_FP32_FUSED_X = {"2d": 5286656 + 0}
+# DRAM read+write per launch of the double-float residual x-pass (ncu, 2-D 511^2); None until captured
+TRAFFIC_DF_TOEP_X = {}
 
 
 def parse():
@@ -344,7 +346,10 @@ def run_ours(args):
     clocks = ClockSampler(local) if rank == 0 else None
     if clocks:
         clocks.start()
-    dom_kind = rfnse.K_TOEP_X if args.workload != "1d" else (rfnse.K_DST | rfnse.K_LAM | rfnse.K_DSCALE | rfnse.K_TOEP_X)
+    # the residual's Toeplitz pass along x (double-float FFTs in the mixed form on these grids); for 1-D
+    # the preconditioner and the product share one FP32 pass
+    dom_kind = (rfnse.K_DF | rfnse.K_TOEP_X) if args.workload != "1d" else \
+        (rfnse.K_FP32 | rfnse.K_DST | rfnse.K_LAM | rfnse.K_DSCALE | rfnse.K_TOEP_X)
     ms, wall, launches, iters_m, _ = timed(mixed, args.steps, args.warmup, clocks=clocks)
     clk = clocks.stop() if clocks else None
     mixed_states = [s.get_state()[1] for s in mixed]   # after warmup + steps, for the FP64 comparison
@@ -386,21 +391,33 @@ def run_ours(args):
     measured = ("CUDA events around every launch of the class (on its stream), serial run of "
                 f"{nprof} further bench steps")
     entries = []
-    if prof and prof[0] > 0:
+    if prof and prof[0] > 0 and args.workload != "1d":
         n, pms, fl, by = prof
-        achieved = fl / (pms * 1e-3) / 1e12
-        peak = FP64_ALU_PEAK_FLOPS / 1e12
-        entries.append({"bound": "alu", "kernel": "k_line_pass<double,F_TOEP_X> (FP64 Toeplitz x-pass)",
-                        "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                        # DRAM read+write of one launch, ncu on the 2-D 511^2 workload
-                        # (profiles/k_line_pass_fp64_toeplitz_x_2d511.md)
-                        "traffic": TRAFFIC_FP64_TOEP_X.get(args.workload), "launches": n,
+        hbm, how = measured_hbm_gbs()
+        achieved = by / (pms * 1e-3) / 1e9
+        fp64eq = fl / (pms * 1e-3) / 1e12
+        entries.append({"bound": "hbm", "kernel": "k_toeplitz_df<F_TOEP_X> (residual Toeplitz x-pass, "
+                                                  "double-float FFTs)",
+                        "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                        # profiles/k_toeplitz_df_x_2d511.md
+                        "traffic": TRAFFIC_DF_TOEP_X.get(args.workload), "launches": n,
                         "avg_launch_us": 1e3 * pms / n, "total_ms": pms,
                         "share_of_step_time": pms / ms_r if ms_r > 0 else None, "measured": measured,
                         "algorithmic_flops_per_launch": fl / n, "algorithmic_bytes_per_launch": by / n,
-                        "achieved_GBps": by / (pms * 1e-3) / 1e9,
-                        "peak_note": "FP64 FMA peak 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz (derived from "
-                                     "the measured 2 FP64 FMA/clk/SM: 1.19 TFLOP/s at 1.995 GHz)"})
+                        "fp64_equivalent_TFLOPs": fp64eq,
+                        "frac_of_fp64_alu_peak": fp64eq * 1e12 / FP64_ALU_PEAK_FLOPS,
+                        "peak_note": f"copy bandwidth, {how} (MEASURED_PEAKS.json).  The FFTs run in "
+                                     "double-float on the FP32 pipes, so their FP64-accurate flop rate may "
+                                     "exceed the native FP64 peak (152 SM x 2 FMA/clk x 2 x 2.07 GHz)"})
+    if prof and prof[0] > 0 and args.workload == "1d":
+        n, pms, fl, by = prof
+        hbm, how = measured_hbm_gbs()
+        achieved = by / (pms * 1e-3) / 1e9
+        entries.append({"bound": "hbm", "kernel": "k_line_pass<float,all flags> (1-D FP32 preconditioner + "
+                                                  "product)", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                        "frac": achieved / hbm, "traffic": None, "launches": n, "avg_launch_us": 1e3 * pms / n,
+                        "total_ms": pms, "share_of_step_time": pms / ms_r if ms_r > 0 else None,
+                        "measured": measured, "peak_note": f"copy bandwidth, {how}"})
     if prof32 and prof32[0] > 0:
         n, pms, fl, by = prof32
         hbm, how = measured_hbm_gbs()

@@ -251,7 +251,9 @@ long long rfnse_launch_count(void);
 int rfnse_probe_fma(int fp64, double* flops_per_s);
 
 /* Kernel classes of rfnse_profile: OR of the operations a line pass fuses, plus RFNSE_K_FP32 for
-   passes computing in FP32.  RFNSE_K_INSCALE is ignored when matching. */
+   passes computing in FP32 and RFNSE_K_DF for the Toeplitz passes of the mixed form's residual, which
+   compute their FFTs in double-float (pairs of FP32 numbers, about 48 significant bits) when every
+   axis has n + 1 in {128, 256, 512, 1024}.  RFNSE_K_INSCALE is ignored when matching. */
 enum {
   RFNSE_K_INSCALE = 1,   /* Arnoldi normalisation v = w / h folded into the load */
   RFNSE_K_DST = 2,       /* DST-I along the axis */
@@ -259,7 +261,8 @@ enum {
   RFNSE_K_DSCALE = 8,    /* (omega I + D) sub-solve of the preconditioner */
   RFNSE_K_TOEP_X = 16,   /* Toeplitz product along x with the diagonal and block coupling */
   RFNSE_K_TOEP_ACC = 32, /* Toeplitz product along y or z, accumulated */
-  RFNSE_K_FP32 = 256
+  RFNSE_K_FP32 = 256,
+  RFNSE_K_DF = 1024
 };
 
 /* Start timing every launch of kernel class `kind` (0 = off) issued by ctx: a CUDA event pair is

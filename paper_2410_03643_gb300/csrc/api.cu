@@ -4,6 +4,7 @@
 #include <new>
 #include <vector>
 #include "internal.cuh"
+#include "fft_fixed.cuh"
 #include "solve.cuh"
 
 using namespace rfnse;
@@ -76,6 +77,10 @@ void free_ctx(rfnse_ctx* c) {
   cudaFree(c->coop_partials);
   cudaFree(c->tape);
   cudaFree(c->adj_red);
+  for (int a = 0; a < 3; ++a) {
+    cudaFree(c->twdf[a]);
+    for (int h = 0; h < 2; ++h) cudaFree(c->circdf[h][a]);
+  }
   for (int a = 0; a < 3; ++a) {
     cudaFree(c->lamC[a]);
     cudaFree(c->chirp64[a]);
@@ -225,6 +230,16 @@ int rfnse_create(const rfnse_params* p, void* stream, rfnse_ctx** out) {
       chk(dalloc(&c->lamfacC32[h], N));
     }
   }
+  if (p->precision == 1) {  // double-float Toeplitz passes of the residual when every axis has a fixed FFT
+    bool all = true;
+    for (int a = 0; a < c->d; ++a) all = all && fixed_fft_length(c->log2L[a]);
+    if (all) {
+      for (int a = 0; a < c->d; ++a) {
+        chk(cudaMalloc(&c->twdf[a], 16 * (size_t)c->L[a]));
+        for (int h = 0; h < 2; ++h) chk(cudaMalloc(&c->circdf[h][a], 8 * (size_t)c->L[a]));
+      }
+    }
+  }
   c->red_blocks = choose_reduce_blocks(N);
   c->use_graphs = p->device_loop != 0;
   c->coop_blocks = coop_blocks_for(N);
@@ -267,6 +282,10 @@ int rfnse_create(const rfnse_params* p, void* stream, rfnse_ctx** out) {
       launch_scale_circ(c->circ[a], c->L[a], hf * c->mu[a] / c->L[a], c->circ64s[h][a], c->circ32s[h][a],
                         c->stream);
   }
+  if (c->twdf[0])
+    for (int a = 0; a < c->d; ++a)
+      launch_setup_df(c->log2L[a], c->circ64s[0][a], c->circ64s[1][a], c->twdf[a], c->circdf[0][a],
+                      c->circdf[1][a], c->stream);
   chk(cudaGetLastError());
   chk(cudaStreamSynchronize(c->stream));
   if (e != cudaSuccess) {

@@ -1,0 +1,73 @@
+// Double-float arithmetic: a value is the unevaluated sum hi + lo of two FP32 numbers with
+// |lo| <= ulp(hi)/2, about 48 significant bits.  Built from two error-free transformations:
+//   TwoSum (Knuth):   s = fl(a + b) and e = (a - (s - bb)) + (b - bb), bb = s - a, give a + b = s + e;
+//   TwoProd with FMA: p = fl(a b) and e = fma(a, b, -p) give a b = p + e exactly.
+// Addition adds the low parts and renormalises with FastTwoSum; multiplication keeps the cross terms
+// hi*lo (the lo*lo term is below the format's precision).  Relative error of one operation is a few
+// units of 2^-48 (for sums of values of opposite sign the bound is relative to |a| + |b|), enough for
+// an FFT whose normwise error is what matters.
+//
+// Used for the Toeplitz products of the mixed form's FP64 residual: GB300 issues FP32 FMA 61 times
+// faster than FP64 FMA, and a double-float FFT costs roughly eight times the FP32 instructions.
+// The compiler must not reassociate these operations (no fast-math).
+#pragma once
+#include "cplx.cuh"
+
+namespace rfnse {
+
+struct dfl {
+  float hi, lo;
+  dfl() = default;
+  __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
+  // from FP64: hi = fl32(x), lo = fl32(x - hi) (exact difference in FP64)
+  __host__ __device__ dfl(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+};
+
+// The additions and the leading product use the _rn intrinsics, which the compiler never contracts into
+// a fused multiply-add: the transformations rely on every one of them being rounded on its own.
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return dfl(s, e);
+}
+__device__ __forceinline__ dfl df_fast_two_sum(float a, float b) {  // requires |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  const float e = __fsub_rn(b, __fsub_rn(s, a));
+  return dfl(s, e);
+}
+__device__ __forceinline__ dfl operator-(dfl a) { return dfl(-a.hi, -a.lo); }
+__device__ __forceinline__ dfl operator+(dfl a, dfl b) {
+  const dfl s = df_two_sum(a.hi, b.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
+__device__ __forceinline__ dfl operator*(dfl a, dfl b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ double df_to_double(dfl a) { return (double)a.hi + (double)a.lo; }
+
+// complex double-float
+struct cdf {
+  dfl x, y;
+};
+template <> struct cvec<dfl> {
+  using type = cdf;
+  static __host__ __device__ __forceinline__ cdf make(dfl a, dfl b) { return cdf{a, b}; }
+};
+
+__device__ __forceinline__ cdf cadd(cdf a, cdf b) { return cdf{a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ cdf csub(cdf a, cdf b) { return cdf{a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ cdf cneg(cdf a) { return cdf{-a.x, -a.y}; }
+__device__ __forceinline__ cdf cmul(cdf a, cdf b) { return cdf{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ __forceinline__ cdf cscale(cdf a, dfl s) { return cdf{a.x * s, a.y * s}; }
+__device__ __forceinline__ cdf cmul_i(cdf a) { return cdf{-a.y, a.x}; }
+__device__ __forceinline__ cdf cmul_mi(cdf a) { return cdf{a.y, -a.x}; }
+__device__ __forceinline__ cdf cdf_from(double2 v) { return cdf{dfl(v.x), dfl(v.y)}; }
+__device__ __forceinline__ double2 cdf_to(cdf v) { return make_double2(df_to_double(v.x), df_to_double(v.y)); }
+
+}  // namespace rfnse

@@ -131,6 +131,13 @@ void launch_rhs_from_tu(const double2* u, const double2* Tu, const double* D, do
 void launch_prep_D(const double* D, float* D32, double2* dfac64, float2* dfac32, double omega, long long N,
                    cudaStream_t s);
 
+// ---- double-float Toeplitz passes (toep_df.cu) --------------------------------------------------
+bool toeplitz_df_available(const rfnse_ctx* c);
+cudaError_t run_toeplitz_df(rfnse_ctx* c, int axis, int half, bool first, const double2* z, const double* D,
+                            const double2* add, double2* w, double2 a, double2 b, const int* skip);
+void launch_setup_df(int log2L, const double* c64h0, const double* c64h1, void* tw, void* c0, void* c1,
+                     cudaStream_t s);
+
 // ---- setup kernels (setup.cu) -------------------------------------------------------------------
 void launch_setup_coefficients(double* c, int nmax, double alpha, cudaStream_t s);
 void launch_setup_axis(const double* c, int n, int L, double* lam, double* circ, double2* tw64, float2* tw32,
@@ -192,6 +199,11 @@ struct rfnse_ctx {
   float2* bspec32[3] = {nullptr, nullptr, nullptr};
   double2* lamfacC64[2] = {nullptr, nullptr};
   float2* lamfacC32[2] = {nullptr, nullptr};
+  // mixed form, double-float Toeplitz products of the residual (toep_df.cu): per axis the fixed-length
+  // FFT's twiddles (complex double-float, 16 B each) and per [half][axis] the scaled circulant spectrum
+  // (double-float, 8 B each); null when some axis has no fixed-length FFT
+  void* twdf[3] = {nullptr, nullptr, nullptr};
+  void* circdf[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
   // mixed form: T u of each history vector, recovered from the final FP64 residual of the solve
   // that produced it (so the right-hand side two steps later needs no Toeplitz product)
   double2* Tu[3] = {nullptr, nullptr, nullptr};

@@ -43,12 +43,19 @@ cudaError_t prepare_D(rfnse_ctx* c, const double* D) {
   return cudaGetLastError();
 }
 
-// w = add + a z + b (T - D) z in FP64 (the Toeplitz products by circulant embedding).
+// w = add + a z + b (T - D) z in FP64 (the Toeplitz products by circulant embedding).  In the mixed
+// form the FFTs of the embedding run in double-float (toep_df.cu) when every axis has a fixed FFT.
 cudaError_t run_matvec_fp64(rfnse_ctx* c, const double2* z, const double* D, double2* w, const double2* add,
                             double2 a, double2 b, int half, const int* skip) {
   cudaStream_t s = c->stream;
   cudaError_t e;
   const int h = half ? 1 : 0;
+  if (c->p.precision == 1 && toeplitz_df_available(c)) {
+    if ((e = run_toeplitz_df(c, 0, h, true, z, D, add, w, a, b, skip)) != cudaSuccess) return e;
+    for (int a2 = 1; a2 < c->d; ++a2)
+      if ((e = run_toeplitz_df(c, a2, h, false, z, nullptr, w, w, a, b, skip)) != cudaSuccess) return e;
+    return cudaSuccess;
+  }
   {
     PassParams p = base_params<double>(c, 0, h);
     p.in = z; p.Dr = D; p.acc_in = add; p.acc_out = w; p.ca = a; p.cb = b; p.skip = skip;

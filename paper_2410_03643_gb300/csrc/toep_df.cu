@@ -1,0 +1,224 @@
+// Toeplitz products of the mixed form's outer residual in double-float arithmetic (dfloat.cuh):
+// w = add + a z + b (mu_a T_0 z - D z) along the first axis and w += b mu_a T_0 z along the others
+// (paper Sec. 2, eq. 'equ2'; the product by circulant embedding as in the FP64 passes), with the two
+// length-L FFTs of the embedding in double-float on the FP32 pipes and the pointwise epilogue in FP64.
+// The FFT is the fixed-length radix-8 Stockham FFT of fft_fixed.cuh instantiated for complex
+// double-float; its twiddles and the scaled circulant spectrum are double-float tables built at set-up.
+// Only for FFT lengths that have a fixed-length FFT (fixed_fft_length); the caller falls back to the
+// FP64 passes otherwise.
+#include <cmath>
+#include "internal.cuh"
+#include "dfloat.cuh"
+#include "fft_fixed.cuh"
+#include "passes.cuh"
+
+namespace rfnse {
+
+template <int LOG2L, bool FIRST>
+__global__ void __launch_bounds__(kPassMaxThreads) k_toeplitz_df(const PassParams p) {
+  using V = cdf;
+  if (p.skip && *p.skip) return;  // uniform
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int L = 1 << LOG2L;
+  constexpr int Nh = L >> 1;
+  const int n = p.n, B = p.B;
+  const int Lp = fft_line_stride(L);
+  V* buf = reinterpret_cast<V*>(smem_raw);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const bool xax = (p.stride == 1);
+  const V zero = cdf{dfl(0.0f, 0.0f), dfl(0.0f, 0.0f)};
+
+  long long line0 = 0, hi = 0, lo0 = 0;
+  if (xax) {
+    line0 = (long long)blockIdx.x * B;
+  } else {
+    hi = (long long)blockIdx.x / p.tiles_inner;
+    lo0 = ((long long)blockIdx.x - hi * p.tiles_inner) * B;
+  }
+  // the tiling of k_line_pass: x lines contiguous, strided tiles of B lines adjacent in x
+  auto map = [&](int e, int& l, int& pos) {
+    if (xax) {
+      if (B == 1) { l = 0; pos = e; }
+      else { l = e / n; pos = e - l * n; }
+    } else {
+      pos = e >> p.log2B;
+      l = e & (B - 1);
+    }
+  };
+  auto gidx = [&](int l, int pos, bool& valid) -> long long {
+    if (xax) {
+      const long long ln = line0 + l;
+      valid = ln < p.nlines;
+      return ln * n + pos;
+    }
+    const long long lo = lo0 + l;
+    valid = lo < p.stride;
+    return lo + (long long)pos * p.stride + hi * p.stride * n;
+  };
+  auto at = [&](int l, int i) -> V& { return buf[(size_t)l * Lp + fft_pad(i)]; };
+
+  // load z into positions 1..n of the embedding, zero the rest
+  const double2* in = reinterpret_cast<const double2*>(p.in);
+  for (int e = tid; e < B * n; e += nthr) {
+    int l, pos;
+    map(e, l, pos);
+    bool valid;
+    const long long g = gidx(l, pos, valid);
+    at(l, 1 + pos) = valid ? cdf_from(in[g]) : zero;
+  }
+  for (int e = tid; e < B * Nh; e += nthr) {  // positions 0 and n+1 .. L-1 (n + 1 = L/2)
+    const int l = e / Nh, k = e - l * Nh;
+    at(l, k == 0 ? 0 : Nh + k) = zero;
+  }
+  for (int l = tid; l < B; l += nthr) at(l, Nh) = zero;
+  __syncthreads();
+
+  const V* tw = reinterpret_cast<const V*>(p.tw);
+  fft_lines_fixed<LOG2L, kFixedLogR, false, true, false>(buf, Lp, B, tw);   // zero upper half in
+  const dfl* circ = reinterpret_cast<const dfl*>(p.circ);
+  for (int e = tid; e < B * L; e += nthr) {
+    const int l = e >> LOG2L, k = e & (L - 1);
+    at(l, k) = cscale(at(l, k), circ[k]);
+  }
+  __syncthreads();
+  fft_lines_fixed<LOG2L, kFixedLogR, true, false, true>(buf, Lp, B, tw);    // lower half out
+
+  // epilogue in FP64: FIRST acc = add + a z + b (t - D z); otherwise acc = acc + b t
+  const double2* accin = reinterpret_cast<const double2*>(p.acc_in);
+  double2* accout = reinterpret_cast<double2*>(p.acc_out);
+  const double* D = reinterpret_cast<const double*>(p.Dr);
+  for (int e = tid; e < B * n; e += nthr) {
+    int l, pos;
+    map(e, l, pos);
+    bool valid;
+    const long long g = gidx(l, pos, valid);
+    if (!valid) continue;
+    double2 t = cdf_to(at(l, 1 + pos));
+    double2 acc = accin ? accin[g] : make_double2(0.0, 0.0);
+    if (FIRST) {
+      const double2 z = in[g];
+      const double Dj = D ? D[g] : 0.0;
+      t.x -= Dj * z.x;
+      t.y -= Dj * z.y;
+      acc = cadd(acc, cmul(p.ca, z));
+    }
+    accout[g] = cadd(acc, cmul(p.cb, t));
+  }
+}
+
+template <int LOG2L>
+static cudaError_t launch_df(rfnse_ctx* c, const PassParams& p, bool first, size_t smem, unsigned grid, int threads,
+                             cudaStream_t s) {
+  auto kern = first ? k_toeplitz_df<LOG2L, true> : k_toeplitz_df<LOG2L, false>;
+  static const cudaError_t attr =
+      [] {
+        cudaError_t e1 = cudaFuncSetAttribute(k_toeplitz_df<LOG2L, true>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaError_t e2 = cudaFuncSetAttribute(k_toeplitz_df<LOG2L, false>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        return e1 != cudaSuccess ? e1 : e2;
+      }();
+  if (attr != cudaSuccess) return attr;
+  kern<<<grid, threads, smem, s>>>(p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+bool toeplitz_df_available(const rfnse_ctx* c) {
+  if (!c->twdf[0]) return false;
+  for (int a = 0; a < c->d; ++a)
+    if (!fixed_fft_length(c->log2L[a])) return false;
+  return true;
+}
+
+// One Toeplitz pass along `axis` in double-float: first = the x-pass with diagonal and coupling.
+cudaError_t run_toeplitz_df(rfnse_ctx* c, int axis, int half, bool first, const double2* z, const double* D,
+                            const double2* add, double2* w, double2 a, double2 b, const int* skip) {
+  PassParams p{};
+  p.n = c->n[axis];
+  p.L = c->L[axis];
+  p.log2L = c->log2L[axis];
+  p.stride = c->stride[axis];
+  p.nlines = c->N / c->n[axis];
+  p.tw = c->twdf[axis];
+  p.circ = c->circdf[half ? 1 : 0][axis];
+  p.in = z;
+  p.Dr = D;
+  p.acc_in = add;
+  p.acc_out = w;
+  p.ca = a;
+  p.cb = b;
+  p.skip = skip;
+  const bool xax = (p.stride == 1);
+  pass_geometry_fixed(p.L, xax, xax ? p.nlines : p.stride, p.nlines, p.nt, p.B);
+  p.log2B = 0;
+  while ((1 << p.log2B) < p.B) ++p.log2B;
+  long long grid;
+  if (xax) {
+    grid = (p.nlines + p.B - 1) / p.B;
+    p.tiles_inner = 1;
+  } else {
+    p.tiles_inner = (p.stride + p.B - 1) / p.B;
+    grid = p.tiles_inner * (p.nlines / p.stride);
+  }
+  if (grid <= 0) return cudaSuccess;
+  if (p.B * p.nt > kPassMaxThreads || p.B * p.nt < 1) return cudaErrorInvalidConfiguration;
+  const size_t smem = (size_t)p.B * fft_line_stride(p.L) * sizeof(cdf);
+  // kernel-class profiling (rfnse_profile): kind = Toeplitz flag | RFNSE_K_DF
+  const int kind = (first ? F_TOEP_X : F_TOEP_ACC) | RFNSE_K_DF;
+  const bool prof = c->prof_kind != 0 && c->prof_kind == kind;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (prof) {
+    while (c->prof_used + 2 > c->prof_events.size()) {
+      cudaEvent_t ev;
+      const cudaError_t e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) return e;
+      c->prof_events.push_back(ev);
+    }
+    e0 = c->prof_events[c->prof_used];
+    e1 = c->prof_events[c->prof_used + 1];
+    c->prof_used += 2;
+    cudaEventRecord(e0, c->stream);
+  }
+  cudaError_t e;
+  switch (p.log2L) {
+    case 8: e = launch_df<8>(c, p, first, smem, (unsigned)grid, p.B * p.nt, c->stream); break;
+    case 9: e = launch_df<9>(c, p, first, smem, (unsigned)grid, p.B * p.nt, c->stream); break;
+    case 10: e = launch_df<10>(c, p, first, smem, (unsigned)grid, p.B * p.nt, c->stream); break;
+    case 11: e = launch_df<11>(c, p, first, smem, (unsigned)grid, p.B * p.nt, c->stream); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (prof) {
+    cudaEventRecord(e1, c->stream);
+    const double lines = (double)p.nlines, N = lines * p.n;
+    c->prof_flops += lines * 2.0 * 5.0 * p.L * p.log2L;  // two FFTs of length L per line
+    c->prof_bytes += N * (16.0 + 16.0 + (add ? 16.0 : 0.0) + ((first && D) ? 8.0 : 0.0));
+  }
+  return e;
+}
+
+// Set-up: the fixed-length FFT's twiddle table in double-float (from FP64 sin/cos of exact binary
+// fractions) and the scaled circulant spectra split into double-float.
+__global__ void k_df_tables(int log2L, const double* __restrict__ c64h0, const double* __restrict__ c64h1,
+                            cdf* __restrict__ tw, dfl* __restrict__ c0, dfl* __restrict__ c1) {
+  const int L = 1 << log2L;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= L) return;
+  int R, ns, r, kk;
+  fixed_twiddle_entry(log2L, kFixedLogR, k, R, ns, r, kk);
+  double sn = 0.0, cs = 1.0;
+  if (R > 1) sincospi(2.0 * (double)(r * kk) / (double)(R * ns), &sn, &cs);
+  tw[k] = cdf{dfl(cs), dfl(-sn)};
+  c0[k] = dfl(c64h0[k]);
+  c1[k] = dfl(c64h1[k]);
+}
+
+void launch_setup_df(int log2L, const double* c64h0, const double* c64h1, void* tw, void* c0, void* c1,
+                     cudaStream_t s) {
+  const int L = 1 << log2L;
+  count_launch();
+  k_df_tables<<<(L + 127) / 128, 128, 0, s>>>(log2L, c64h0, c64h1, reinterpret_cast<cdf*>(tw),
+                                              reinterpret_cast<dfl*>(c0), reinterpret_cast<dfl*>(c1));
+}
+
+}  // namespace rfnse

@@ -58,7 +58,7 @@ EXPORTED = ("rfnse_default_params", "rfnse_create", "rfnse_destroy", "rfnse_last
             "rfnse_batch_destroy", "rfnse_batch_last_error", "rfnse_batch_context", "rfnse_batch_run",
             "rfnse_tape_forward", "rfnse_tape_backward", "rfnse_adjoint_solve", "rfnse_tban_solve")
 
-K_INSCALE, K_DST, K_LAM, K_DSCALE, K_TOEP_X, K_TOEP_ACC, K_FP32 = 1, 2, 4, 8, 16, 32, 256
+K_INSCALE, K_DST, K_LAM, K_DSCALE, K_TOEP_X, K_TOEP_ACC, K_FP32, K_DF = 1, 2, 4, 8, 16, 32, 256, 1024
 
 _lib = None
 

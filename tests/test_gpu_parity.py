@@ -301,3 +301,27 @@ def test_config_2d_511_first_steps(alpha, precision):
         assert rel(got[k], ref[k]) < (1e-10 if precision == 0 else 1e-8), (k, rel(got[k], ref[k]))
         if precision == 0:
             assert abs(int(iters[k]) - its_ref[k]) <= 1
+
+
+DF_CASES = [
+    W.Problem(d=1, n=(1023,), lo=(-20.0,), hi=(20.0,), alpha=1.5, rho=2.0, dt=0.01),
+    W.Problem(d=2, n=(127, 255), lo=(-6.0, -8.0), hi=(6.0, 8.0), alpha=1.3, rho=2.0, dt=0.01),
+    W.Problem(d=3, n=(127, 127, 127), lo=(-4.0,) * 3, hi=(4.0,) * 3, alpha=1.8, rho=1.0, dt=0.01),
+]
+
+
+@pytest.mark.parametrize("half", (False, True))
+@pytest.mark.parametrize("p", DF_CASES, ids=["1d1023", "2d127x255", "3d127"])
+def test_double_float_residual_products_match_fp64(p, half):
+    """In the mixed form the Toeplitz products of the FP64 residual run their FFTs in double-float when
+    every axis has n + 1 in {128..1024}: the system matrix applied by a mixed context agrees with the
+    FP64 context's to the double-float FFT's normwise error."""
+    u = dev(W.random_field(p.shape, 51))
+    D = dev(diag_D(W.random_field(p.shape, 52), p.rho, p.dt))
+    s64 = Solver(p, precision=0)
+    sdf = Solver(p, precision=1)
+    want = host(s64.apply_A(u, D, half), p.shape)
+    got = host(sdf.apply_A(u, D, half), p.shape)
+    assert rel(got, want) < 2e-13
+    s64.close()
+    sdf.close()
