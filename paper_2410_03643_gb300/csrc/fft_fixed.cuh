@@ -24,6 +24,9 @@ namespace rfnse {
 // this layout for these lengths.
 __host__ __device__ constexpr bool fixed_fft_length(int log2L) { return log2L >= 8 && log2L <= 11; }
 constexpr int kFixedLogR = 3;
+// The double-float Toeplitz passes (toep_df.cu) use radix 4 (L/4 threads per line): their butterflies
+// hold four times the registers of FP32 ones, and the extra threads measured faster on both workloads.
+constexpr int kFixedLogRDF = 2;
 
 template <int LOG2L, int LOGR>
 struct FixedPlan {

@@ -392,12 +392,13 @@ inline void pass_geometry(int L, bool xax, long long lines_avail, int& nt, int& 
   while (B > 1 && B > lines_avail) B >>= 1;  // keep B a power of two
 }
 
-// The fixed-length FFT: L / 2^kFixedLogR threads per line; blocks of up to 128 threads along x and 256
+// The fixed-length FFT: L / 2^logR threads per line; blocks of up to 128 threads along x and 256
 // along a strided axis (B lines adjacent in x, so B >= 2 keeps 16-byte runs per row), with fewer lines
 // per block while that leaves fewer than two blocks per SM (152 SMs).  Measured on the 2-D 511^2 and
 // 3-D 255^3 workloads against 1..4 lines per block on each axis.
-inline void pass_geometry_fixed(int L, bool xax, long long lines_avail, long long nlines, int& nt, int& B) {
-  nt = L >> kFixedLogR;
+inline void pass_geometry_fixed(int L, bool xax, long long lines_avail, long long nlines, int& nt, int& B,
+                                int logR = kFixedLogR) {
+  nt = L >> logR;
   B = (xax ? 128 : 256) / nt;
   if (B < 1) B = 1;
   while (B > 1 && B * nt > kPassMaxThreads) B >>= 1;

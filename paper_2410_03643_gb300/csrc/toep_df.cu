@@ -2,8 +2,8 @@
 // w = add + a z + b (mu_a T_0 z - D z) along the first axis and w += b mu_a T_0 z along the others
 // (paper Sec. 2, eq. 'equ2'; the product by circulant embedding as in the FP64 passes), with the two
 // length-L FFTs of the embedding in double-float on the FP32 pipes and the pointwise epilogue in FP64.
-// The FFT is the fixed-length radix-8 Stockham FFT of fft_fixed.cuh instantiated for complex
-// double-float; its twiddles and the scaled circulant spectrum are double-float tables built at set-up.
+// The FFT is the fixed-length Stockham FFT of fft_fixed.cuh (radix kFixedLogRDF) instantiated for
+// complex double-float; its twiddles and the scaled circulant spectrum are double-float tables built at set-up.
 // Only for FFT lengths that have a fixed-length FFT (fixed_fft_length); the caller falls back to the
 // FP64 passes otherwise.
 #include <cmath>
@@ -74,14 +74,14 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_toeplitz_df(const PassParam
   __syncthreads();
 
   const V* tw = reinterpret_cast<const V*>(p.tw);
-  fft_lines_fixed<LOG2L, kFixedLogR, false, true, false>(buf, Lp, B, tw);   // zero upper half in
+  fft_lines_fixed<LOG2L, kFixedLogRDF, false, true, false>(buf, Lp, B, tw);   // zero upper half in
   const dfl* circ = reinterpret_cast<const dfl*>(p.circ);
   for (int e = tid; e < B * L; e += nthr) {
     const int l = e >> LOG2L, k = e & (L - 1);
     at(l, k) = cscale(at(l, k), circ[k]);
   }
   __syncthreads();
-  fft_lines_fixed<LOG2L, kFixedLogR, true, false, true>(buf, Lp, B, tw);    // lower half out
+  fft_lines_fixed<LOG2L, kFixedLogRDF, true, false, true>(buf, Lp, B, tw);    // lower half out
 
   // epilogue in FP64: FIRST acc = add + a z + b (t - D z); otherwise acc = acc + b t
   const double2* accin = reinterpret_cast<const double2*>(p.acc_in);
@@ -150,7 +150,7 @@ cudaError_t run_toeplitz_df(rfnse_ctx* c, int axis, int half, bool first, const 
   p.cb = b;
   p.skip = skip;
   const bool xax = (p.stride == 1);
-  pass_geometry_fixed(p.L, xax, xax ? p.nlines : p.stride, p.nlines, p.nt, p.B);
+  pass_geometry_fixed(p.L, xax, xax ? p.nlines : p.stride, p.nlines, p.nt, p.B, kFixedLogRDF);
   p.log2B = 0;
   while ((1 << p.log2B) < p.B) ++p.log2B;
   long long grid;
@@ -205,7 +205,7 @@ __global__ void k_df_tables(int log2L, const double* __restrict__ c64h0, const d
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= L) return;
   int R, ns, r, kk;
-  fixed_twiddle_entry(log2L, kFixedLogR, k, R, ns, r, kk);
+  fixed_twiddle_entry(log2L, kFixedLogRDF, k, R, ns, r, kk);
   double sn = 0.0, cs = 1.0;
   if (R > 1) sincospi(2.0 * (double)(r * kk) / (double)(R * ns), &sn, &cs);
   tw[k] = cdf{dfl(cs), dfl(-sn)};
