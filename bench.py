@@ -59,8 +59,8 @@ def measured_hbm_gbs():
 
 # DRAM read+write per launch of the FP32 fused DST-x + (wI+D) + Toeplitz-x pass (ncu, 2-D 511^2)
 TRAFFIC_FP32_FUSED_X = {"2d": 5286656 + 0}
-# DRAM read+write per launch of the double-float residual x-pass (ncu, 2-D 511^2); None until captured
-TRAFFIC_DF_TOEP_X = {}
+# DRAM read+write per launch of the double-float residual x-pass (ncu, 2-D 511^2, steady launch)
+TRAFFIC_DF_TOEP_X = {"2d": 6368768 + 0}
 
 
 def parse():

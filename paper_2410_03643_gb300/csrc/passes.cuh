@@ -84,6 +84,9 @@ struct PassParams {
   const void* chirp;
   const void* bspec;
   int inv_dft;
+  // double-float Toeplitz passes: ca and cb as codes when they are 0, +-1 or +-i (products become
+  // swaps and sign changes), -1 otherwise
+  int ca_code, cb_code;
 };
 
 template <typename R> __device__ __forceinline__ cv<R> ld_c(const void* p, long long i);

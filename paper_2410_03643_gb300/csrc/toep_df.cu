@@ -14,6 +14,27 @@
 
 namespace rfnse {
 
+// c v for a coefficient given by code (0: 0, 1: +1, 2: -1, 3: +i, 4: -i) or, for code -1, in full
+__device__ __forceinline__ double2 coef_mul(int code, double2 c, double2 v) {
+  switch (code) {
+    case 0: return make_double2(0.0, 0.0);
+    case 1: return v;
+    case 2: return make_double2(-v.x, -v.y);
+    case 3: return make_double2(-v.y, v.x);
+    case 4: return make_double2(v.y, -v.x);
+    default: return cmul(c, v);
+  }
+}
+
+static int coef_code(double2 c) {
+  if (c.x == 0.0 && c.y == 0.0) return 0;
+  if (c.x == 1.0 && c.y == 0.0) return 1;
+  if (c.x == -1.0 && c.y == 0.0) return 2;
+  if (c.x == 0.0 && c.y == 1.0) return 3;
+  if (c.x == 0.0 && c.y == -1.0) return 4;
+  return -1;
+}
+
 template <int LOG2L, bool FIRST>
 __global__ void __launch_bounds__(kPassMaxThreads) k_toeplitz_df(const PassParams p) {
   using V = cdf;
@@ -100,9 +121,9 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_toeplitz_df(const PassParam
       const double Dj = D ? D[g] : 0.0;
       t.x -= Dj * z.x;
       t.y -= Dj * z.y;
-      acc = cadd(acc, cmul(p.ca, z));
+      acc = cadd(acc, coef_mul(p.ca_code, p.ca, z));
     }
-    accout[g] = cadd(acc, cmul(p.cb, t));
+    accout[g] = cadd(acc, coef_mul(p.cb_code, p.cb, t));
   }
 }
 
@@ -148,6 +169,8 @@ cudaError_t run_toeplitz_df(rfnse_ctx* c, int axis, int half, bool first, const 
   p.acc_out = w;
   p.ca = a;
   p.cb = b;
+  p.ca_code = coef_code(a);
+  p.cb_code = coef_code(b);
   p.skip = skip;
   const bool xax = (p.stride == 1);
   pass_geometry_fixed(p.L, xax, xax ? p.nlines : p.stride, p.nlines, p.nt, p.B, kFixedLogRDF);
