@@ -241,6 +241,14 @@ int rfnse_apply_prec_static(const rfnse_params* p, const void* v, void* z, const
 
 /* ---- instrumentation -------------------------------------------------------------------------- */
 
+/* Self-test of the bounded device-side waits (the grid-wide barrier of the cooperative Arnoldi kernel,
+   which the paper does not have): one block waits at a barrier that nothing will release; the wait
+   must give up after its poll limit, set its error flag and let the kernel finish, so the context
+   stays usable.  *err (host) receives the flag (1 = the wait gave up, as it must); *ms (host, may be
+   NULL) the kernel's duration.  stream: cudaStream_t (may be NULL); the call synchronises it.
+   Allocates and frees a few bytes of device memory.  Errors: EINVAL, ENOMEM, ECUDA. */
+int rfnse_selftest_bounded_wait(void* stream, int* err, double* ms);
+
 /* Number of CUDA kernels this library has launched in the calling process (all contexts). */
 long long rfnse_launch_count(void);
 

@@ -445,4 +445,48 @@ void launch_resid_update(const double2* V, long long ldv, const double2* w, cons
   k_resid_update<<<ew_blocks_c(N), 256, 0, s>>>(V, ldv, w, gs, k, r, N);
 }
 
+// Self-test of the bounded wait: one block arrives at a grid barrier whose arrival count is preset so
+// that the barrier can never complete (a release that nothing performs); grid_barrier must give up
+// after kMaxSpin polls, record the failure and return.
+__global__ void k_selftest_wait(GridBarrier* b, int* err) { grid_barrier(b, err); }
+
 }  // namespace rfnse
+
+extern "C" int rfnse_selftest_bounded_wait(void* stream, int* err, double* ms) {
+  using namespace rfnse;
+  if (!err) return RFNSE_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  GridBarrier* b = nullptr;
+  int* d_err = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int st = RFNSE_OK;
+  const GridBarrier init = {1u, 0u};  // one phantom arrival: the single block's arrival makes 2 of 1
+  if (cudaMalloc(&b, sizeof(GridBarrier)) != cudaSuccess || cudaMalloc(&d_err, sizeof(int)) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    st = RFNSE_ENOMEM;
+  } else if (cudaMemcpyAsync(b, &init, sizeof(init), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+             cudaMemsetAsync(d_err, 0, sizeof(int), s) != cudaSuccess) {
+    st = RFNSE_ECUDA;
+  } else {
+    cudaEventRecord(e0, s);
+    k_selftest_wait<<<1, 32, 0, s>>>(b, d_err);
+    count_launch();
+    cudaEventRecord(e1, s);
+    int h = 0;
+    if (cudaGetLastError() != cudaSuccess || cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+                                                 cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      st = RFNSE_ECUDA;
+    } else {
+      *err = h;
+      float t = 0.0f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (ms) *ms = t;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(b);
+  cudaFree(d_err);
+  return st;
+}

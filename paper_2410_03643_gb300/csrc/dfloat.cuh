@@ -49,7 +49,30 @@ __device__ __forceinline__ dfl operator*(dfl a, dfl b) {
   e = fmaf(a.lo, b.hi, e);
   return df_fast_two_sum(p, e);
 }
-__device__ __forceinline__ double df_to_double(dfl a) { return (double)a.hi + (double)a.lo; }
+// Conversions with few FP64 instructions (GB300's FP64 pipe is the scarce one).  float -> double of a
+// normal float is exact bit manipulation (sign, rebiased exponent, significand shifted left by 29);
+// zeros, subnormals, infinities and NaNs take the hardware conversion.
+__device__ __forceinline__ double df_f2d(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e8 = (b >> 23) & 0xffu;
+  if (e8 == 0u || e8 == 0xffu) return (double)f;
+  const unsigned long long d = ((unsigned long long)(b & 0x80000000u) << 32) |
+                               ((unsigned long long)(e8 + (1023u - 127u)) << 52) |
+                               ((unsigned long long)(b & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)d);
+}
+// double -> double-float: hi = x with its significand truncated to 24 bits (integer work when x is in
+// the normal float range), lo = fl32(x - hi) (one exact FP64 subtraction and one conversion).
+__device__ __forceinline__ dfl df_split(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  if (e >= 255) return dfl((float)x, 0.0f);  // beyond the float range: +-inf (or NaN) in hi alone
+  if (e <= 0) return dfl(x);                 // zero and tiny values: the FP64 path
+  const double hd = __longlong_as_double((long long)(b & 0xFFFFFFFFE0000000ull));
+  const unsigned hb = (unsigned)(b >> 32 & 0x80000000ull) | ((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7fffffull);
+  return dfl(__uint_as_float(hb), __double2float_rn(x - hd));
+}
+__device__ __forceinline__ double df_to_double(dfl a) { return df_f2d(a.hi) + df_f2d(a.lo); }
 
 // complex double-float
 struct cdf {
@@ -67,7 +90,7 @@ __device__ __forceinline__ cdf cmul(cdf a, cdf b) { return cdf{a.x * b.x - a.y *
 __device__ __forceinline__ cdf cscale(cdf a, dfl s) { return cdf{a.x * s, a.y * s}; }
 __device__ __forceinline__ cdf cmul_i(cdf a) { return cdf{-a.y, a.x}; }
 __device__ __forceinline__ cdf cmul_mi(cdf a) { return cdf{a.y, -a.x}; }
-__device__ __forceinline__ cdf cdf_from(double2 v) { return cdf{dfl(v.x), dfl(v.y)}; }
+__device__ __forceinline__ cdf cdf_from(double2 v) { return cdf{df_split(v.x), df_split(v.y)}; }
 __device__ __forceinline__ double2 cdf_to(cdf v) { return make_double2(df_to_double(v.x), df_to_double(v.y)); }
 
 }  // namespace rfnse

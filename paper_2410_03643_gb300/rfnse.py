@@ -56,7 +56,8 @@ EXPORTED = ("rfnse_default_params", "rfnse_create", "rfnse_destroy", "rfnse_last
             "rfnse_dst", "rfnse_toeplitz", "rfnse_solve", "rfnse_get_coefficients", "rfnse_launch_count",
             "rfnse_profile", "rfnse_profile_read", "rfnse_probe_fma", "rfnse_batch_create",
             "rfnse_batch_destroy", "rfnse_batch_last_error", "rfnse_batch_context", "rfnse_batch_run",
-            "rfnse_tape_forward", "rfnse_tape_backward", "rfnse_adjoint_solve", "rfnse_tban_solve")
+            "rfnse_tape_forward", "rfnse_tape_backward", "rfnse_adjoint_solve", "rfnse_tban_solve",
+            "rfnse_selftest_bounded_wait")
 
 K_INSCALE, K_DST, K_LAM, K_DSCALE, K_TOEP_X, K_TOEP_ACC, K_FP32, K_DF = 1, 2, 4, 8, 16, 32, 256, 1024
 
@@ -127,6 +128,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.rfnse_adjoint_solve.restype = ip
     lib.rfnse_tban_solve.argtypes = [vp, vp, vp, vp, ip, ctypes.POINTER(ctypes.c_int), dp]
     lib.rfnse_tban_solve.restype = ip
+    lib.rfnse_selftest_bounded_wait.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp]
+    lib.rfnse_selftest_bounded_wait.restype = ip
     if path == _build.library_path():
         _lib = lib
     return lib
@@ -155,6 +158,18 @@ def make_params(problem, precision: int = 0, inner_tol: float = 1e-6, max_outer:
     p.device_loop = device_loop
     p.precond = getattr(problem, "precond", 0)
     return p
+
+
+def selftest_bounded_wait(stream=None):
+    """Run the bounded-wait self-test: returns (error flag, kernel ms); the flag must be 1."""
+    lib = load_library()
+    err = ctypes.c_int(0)
+    ms = ctypes.c_double(0.0)
+    st = lib.rfnse_selftest_bounded_wait(ctypes.c_void_p(stream.cuda_stream) if stream is not None else None,
+                                         ctypes.byref(err), ctypes.byref(ms))
+    if st != RFNSE_OK:
+        raise RfnseError(st, "bounded-wait self-test failed to run")
+    return err.value, ms.value
 
 
 def launch_count() -> int:

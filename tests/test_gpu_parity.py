@@ -325,3 +325,17 @@ def test_double_float_residual_products_match_fp64(p, half):
     assert rel(got, want) < 2e-13
     s64.close()
     sdf.close()
+
+
+def test_bounded_device_wait_gives_up_and_the_context_stays_usable():
+    """A grid barrier that nothing releases: the wait gives up after its poll limit and sets the error
+    flag (RFNSE_ETIMEOUT in a solve); the device and a solver context keep working afterwards."""
+    from paper_2410_03643_gb300.rfnse import selftest_bounded_wait
+    err, ms = selftest_bounded_wait()
+    assert err == 1
+    assert 0.0 < ms < 20000.0
+    p = SMALL[2].replace(tol=1e-10)
+    s = Solver(p)
+    u, it, rr = s.solve(dev(np.zeros(p.shape)), dev(W.random_field(p.shape, 61)))
+    assert rr < p.tol and it >= 1
+    s.close()
