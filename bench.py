@@ -3,8 +3,9 @@
 
 Workload (default): d = 2, n = 511 x 511 on [-10,10]^2, rho = 2, dt = 0.005, u0 = sech(x)sech(y)e^{i(x+y)},
 alpha in {1.2, 1.5, 1.9} (three independent instances), tol 1e-10.  One bench step advances all three
-instances by one time step (a GMRES solve each) in the mixed form (FP32 transforms inside FGMRES,
-FP64 Arnoldi/Givens and FP64 outer residual); the plain FP64 form is timed the same way and reported
+instances by one time step (a GMRES solve each, all three through one rfnse_batch_run call) in the mixed
+form (FP32 transforms inside FGMRES, FP64 Arnoldi/Givens, the refinement residual accurate to about
+1e-14); the plain FP64 form is timed the same way and reported
 beside it, with the difference between the two trajectories.  DOF = complex grid unknowns.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -280,10 +281,19 @@ def run_ours(args):
     main = torch.cuda.current_stream()
     concurrent = not args.serial and len(inst) > 1
     pool = ThreadPoolExecutor(max_workers=len(inst)) if concurrent else None
+    # several instances advance together through the batch API (one graph launch per step for all);
+    # host-driven loops (--host-loop, for kernel profilers) keep one host thread per instance
+    use_batch = concurrent and not args.host_loop
 
-    def make(precision, device_loop=None):
+    def make(precision, device_loop=None, batch=None):
         if device_loop is None:
             device_loop = 0 if args.host_loop else 1
+        if use_batch if batch is None else batch:
+            b = rfnse.Batch([p for p, _ in inst], precision=precision, stream=main, device_loop=device_loop)
+            for i, (p, u0) in enumerate(inst):
+                b.set_state(i, torch.from_numpy(u0.ravel().copy()).to(dev))
+            torch.cuda.synchronize()
+            return b
         solvers = []
         for p, u0 in inst:
             st = torch.cuda.Stream(device=dev) if concurrent else main
@@ -295,6 +305,8 @@ def run_ours(args):
 
     def advance(solvers, start_ev=None, serial=False):
         """One bench step: every instance advances one time step (instances in parallel streams)."""
+        if isinstance(solvers, rfnse.Batch):
+            return [int(v) for v in solvers.run(1)[0][0]]
         if serial or not concurrent:
             return [int(s.run(1)[0][0]) for s in solvers]
         if start_ev is not None:
@@ -306,6 +318,18 @@ def run_ours(args):
             ev.record(s.stream)
             main.wait_event(ev)
         return its
+
+    def states_of(group):
+        if isinstance(group, rfnse.Batch):
+            return [group.get_state(i)[1] for i in range(group.count)]
+        return [s.get_state()[1] for s in group]
+
+    def close_all(group):
+        if isinstance(group, rfnse.Batch):
+            group.close()
+        else:
+            for s in group:
+                s.close()
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     dof_per_step = sum(p.size for p, _ in inst)
@@ -358,13 +382,13 @@ def run_ours(args):
         (rfnse.K_FP32 | rfnse.K_DST | rfnse.K_LAM | rfnse.K_DSCALE | rfnse.K_TOEP_X)
     ms, wall, launches, iters_m, _ = timed(mixed, args.steps, args.warmup, clocks=clocks)
     clk = clocks.stop() if clocks else None
-    mixed_states = [s.get_state()[1] for s in mixed]   # after warmup + steps, for the FP64 comparison
+    mixed_states = states_of(mixed)   # after warmup + steps, for the FP64 comparison
     # the dominant kernel class, timed launch by launch in a further serial run of the same steps
     # (in the concurrent region the instances' kernels share the SMs, which stretches each launch)
     # (host-driven solvers: CUDA events cannot be recorded around single kernels inside a running graph;
     # the kernels are the same as in the device loop)
     nprof = max(1, min(args.steps, 20))
-    prof_solvers = make(1, device_loop=0)
+    prof_solvers = make(1, device_loop=0, batch=False)
     ms_r, _, _, _, prof = timed(prof_solvers, nprof, args.warmup, profile_kind=dom_kind, serial=True)
     for s in prof_solvers:
         s.close()
@@ -372,7 +396,7 @@ def run_ours(args):
     prof32 = None
     if args.workload in ("2d", "3d"):
         k32 = rfnse.K_FP32 | rfnse.K_DST | rfnse.K_DSCALE | rfnse.K_TOEP_X
-        prof_solvers = make(1, device_loop=0)
+        prof_solvers = make(1, device_loop=0, batch=False)
         ms_r32, _, _, _, prof32 = timed(prof_solvers, nprof, args.warmup, profile_kind=k32, serial=True)
         for s in prof_solvers:
             s.close()
@@ -386,7 +410,9 @@ def run_ours(args):
            "config": dict(desc, precision="mixed: FP32 transforms in FGMRES, FP64 Arnoldi/Givens/residual",
                           l2="256 MiB buffer written between timed steps",
                           parallelism=(f"{world} GPU(s), instances replicated per GPU; "
-                                       + ("one CUDA stream and host thread per instance" if concurrent
+                                       + ("all instances advanced by one batch call per step "
+                                          "(rfnse_batch_run: one CUDA graph launch)" if use_batch else
+                                          "one CUDA stream and host thread per instance" if concurrent
                                           else "instances in turn on one stream")),
                           control=("host-driven GMRES loops" if args.host_loop
                                    else "device-decided GMRES loops, one CUDA graph per solve")),
@@ -454,19 +480,17 @@ def run_ours(args):
         ms64, _, _, iters64, _ = timed(fp64, args.steps, args.warmup)
         ms64 = reduce_max(ms64, world, dev)
         errs = []
-        for ua, b in zip(mixed_states, fp64):
-            _, ub, _ = b.get_state()
+        for ua, ub in zip(mixed_states, states_of(fp64)):
             errs.append(float(torch.linalg.vector_norm(ua - ub) / torch.linalg.vector_norm(ub)))
         out["fp64"] = {"value": world * dof_per_step * args.steps / (ms64 * 1e-3), "ms_per_step": ms64 / args.steps,
                        "iters_per_solve_mean": float(np.mean(iters64)) if iters64 else None}
         out["mixed_vs_fp64_rel_l2_after_run"] = max(errs)
         out["mixed_speedup_vs_fp64"] = ms64 / ms_max
-        for s in fp64:
-            s.close()
+        close_all(fp64)
 
     # end to end through the C ABI with host buffers: H2D of the step's inputs, D2H of its result
     if not args.no_e2e:
-        e2e_solvers = make(1)
+        e2e_solvers = make(1, batch=False)
         for s in e2e_solvers:
             s.run(2)  # reach a regular step
         hosts = []
@@ -510,8 +534,7 @@ def run_ours(args):
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                                "sample": f"{n} time steps of the alpha={inst[0][0].alpha} instance "
                                          f"({secs:.1f} s), numpy/BLAS dense-transform oracle"}
-    for s in mixed:
-        s.close()
+    close_all(mixed)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
