@@ -378,7 +378,11 @@ int coop_blocks_for(long long N) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mgs_step, kCtlThreads, 0);
-  long long b = (long long)sms * (per_sm < 2 ? per_sm : 2);
+  // Small grids (up to a few 10^5 points) are bound by the barriers between the MGS passes: one block
+  // per SM is faster and leaves room for other instances' kernels; large grids stream their vectors
+  // and take two blocks per SM (measured on the 2-D 511^2, batched and 3-D 255^3 workloads).
+  const int use = (N >= (1LL << 22)) ? 2 : 1;
+  long long b = (long long)sms * (per_sm < use ? per_sm : use);
   const long long need = (N + kCtlThreads - 1) / kCtlThreads;
   if (b > need) b = need;
   if (b < 1) b = 1;
