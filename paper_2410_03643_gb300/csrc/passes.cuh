@@ -98,8 +98,9 @@ template <> __device__ __forceinline__ float2 ld_c<float>(const void* p, long lo
 }
 
 // FP32 passes whose FFT length passes fixed_fft_length (fft_fixed.cuh) are compiled with the length
-// fixed (radix-8 register butterflies, twiddles read from the global per-stage table through L1); all
-// other passes use the runtime-length radix-4 FFT of fft_line.cuh with the table in shared memory.
+// fixed (radix-8 register butterflies; k_line_pass_fixed below, or for the Bluestein passes of the
+// circulant comparator this kernel with the twiddles read from the global per-stage table through L1);
+// all other passes use the runtime-length radix-4 FFT of fft_line.cuh with the table in shared memory.
 template <int LOG2L, bool INV, bool ZU, bool HO, typename V>
 __device__ __forceinline__ void fft_any(V* buf, int Lp, int L, int log2L, int nt, int B, const V* tw) {
   if constexpr (LOG2L > 0) {
@@ -384,6 +385,270 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_line_pass(const PassParams 
   }
 }
 
+// FP32 passes whose FFT length is fixed at compile time (fixed_fft_length), every operation of
+// k_line_pass but the circulant comparator's Bluestein DFTs.  Same tiles and geometry (B lines,
+// T = L/8 threads per line, B T threads), so with n = L/2 - 1 a thread owns at most QN = L/(2T) points
+// of the tile and QL = L/T of its B L spectrum positions: the per-point loops are unrolled over these
+// slots.  Every global operand (input, D, dfac, lamfac, accumulator, z_add target, circulant
+// eigenvalues, twiddles) is loaded into registers in one batch at the start, so the pass waits on
+// global memory once rather than once per loop iteration and FFT stage; the twiddles are then staged in
+// shared memory, and z stays in registers between the sub-solve and the Toeplitz epilogue.
+template <typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS, int LOG2L>
+__global__ void __launch_bounds__(kPassMaxThreads) k_line_pass_fixed(const PassParams p) {
+  static_assert(!(FLAGS & F_CIRC), "the circulant comparator's passes run in k_line_pass");
+  static_assert(LOG2L > 0, "fixed FFT length only");
+  using R = float;
+  using V = float2;
+  using P = FixedPlan<LOG2L, kFixedLogR>;
+  constexpr int L = P::L, Nh = L / 2, T = P::T;
+  constexpr int QN = (Nh + T - 1) / T;
+  constexpr int QL = L / T;
+  constexpr bool TOEP = (FLAGS & (F_TOEP_X | F_TOEP_ACC)) != 0;
+  if (p.skip && *p.skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = p.n, B = p.B;
+  const int Lp = fft_line_stride(L);
+  V* buf = reinterpret_cast<V*>(smem_raw);
+  V* tws = buf + (size_t)B * Lp;  // the L - 1 entries of the per-stage twiddle table
+  const int tid = threadIdx.x, nthr = B * T;
+  const bool xax = (p.stride == 1);
+  const V zero = make_float2(0.f, 0.f);
+
+  long long line0 = 0, hi = 0, lo0 = 0;
+  if (xax) {
+    line0 = (long long)blockIdx.x * B;
+  } else {
+    hi = (long long)blockIdx.x / p.tiles_inner;
+    lo0 = ((long long)blockIdx.x - hi * p.tiles_inner) * B;
+  }
+  // slot q of this thread: tile element e = tid + q B T -> line l, position pos, global index g
+  int sl[QN], sp[QN];
+  long long sg[QN];
+  bool sin_[QN], sok[QN];  // in the tile (e < B n); also in the grid
+#pragma unroll
+  for (int q = 0; q < QN; ++q) {
+    const int e = tid + q * nthr;
+    int l = 0, pos = 0;
+    if (xax) {
+      if (B == 1) pos = e;
+      else { l = e / n; pos = e - l * n; }
+    } else {
+      pos = e >> p.log2B;
+      l = e & (B - 1);
+    }
+    bool valid;
+    long long g;
+    if (xax) {
+      const long long ln = line0 + l;
+      valid = ln < p.nlines;
+      g = ln * n + pos;
+    } else {
+      const long long lo = lo0 + l;
+      valid = lo < p.stride;
+      g = lo + (long long)pos * p.stride + hi * p.stride * n;
+    }
+    sin_[q] = e < B * n;
+    sok[q] = sin_[q] && valid;
+    sl[q] = l;
+    sp[q] = pos;
+    sg[q] = g;
+  }
+  auto at = [&](int l, int i) -> V& { return buf[(size_t)l * Lp + fft_pad(i)]; };
+
+  // ---- every global operand, one batch ---------------------------------------------------------
+  V twr[QL];
+  {
+    const V* twg = reinterpret_cast<const V*>(p.tw);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+      const int i = tid + q * nthr;
+      if (i < L - 1) twr[q] = __ldg(twg + i);
+    }
+  }
+  [[maybe_unused]] R cq[QL];
+  if constexpr (TOEP) {
+    const R* circ = reinterpret_cast<const R*>(p.circ);
+#pragma unroll
+    for (int q = 0; q < QL; ++q) cq[q] = __ldg(circ + ((tid + q * nthr) & (L - 1)));
+  }
+  V xq[QN];
+  {
+    const TIN* in = reinterpret_cast<const TIN*>(p.in);
+    if (p.gdyn && p.in_dyn_z) in = reinterpret_cast<const TIN*>(p.zbase) + (long long)p.gdyn->j * p.ldv;
+    const double2* src = reinterpret_cast<const double2*>(p.in);
+    double2* cpy = p.copy_out;
+    double sc = 1.0;
+    if constexpr ((FLAGS & F_INSCALE) != 0) {
+      if (p.gdyn) {
+        src = p.gdyn->src;
+        sc = p.gdyn->src_scale;
+        cpy = p.vbase + (long long)p.gdyn->j * p.ldv;
+      } else {
+        sc = *p.in_scale;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < QN; ++q) {
+      xq[q] = zero;
+      if (sok[q]) {
+        if constexpr ((FLAGS & F_INSCALE) != 0) {
+          double2 vd = __ldg(src + sg[q]);
+          vd.x *= sc;
+          vd.y *= sc;
+          cpy[sg[q]] = vd;
+          xq[q] = to_c<R>(vd);
+        } else {
+          xq[q] = to_c<R>(__ldg(in + sg[q]));
+        }
+      }
+    }
+  }
+  [[maybe_unused]] V fq[QN], lq[QN], aq[QN], oq[QN];
+  [[maybe_unused]] R dq[QN];
+  [[maybe_unused]] TOUT* zout = reinterpret_cast<TOUT*>(p.out);
+  if constexpr ((FLAGS & F_DSCALE) != 0) {
+    if (p.gdyn && p.zbase) zout = reinterpret_cast<TOUT*>(p.zbase) + (long long)p.gdyn->j * p.ldv;
+    const V* dfac = reinterpret_cast<const V*>(p.dfac);
+#pragma unroll
+    for (int q = 0; q < QN; ++q) {
+      fq[q] = (dfac && sok[q]) ? __ldg(dfac + sg[q]) : make_float2(1.f, 0.f);
+      oq[q] = (zout && p.z_add && sok[q]) ? to_c<R>(zout[sg[q]]) : zero;
+    }
+  }
+  if constexpr ((FLAGS & F_LAM) != 0) {
+    const V* lam = reinterpret_cast<const V*>(p.lamfac);
+#pragma unroll
+    for (int q = 0; q < QN; ++q) lq[q] = sok[q] ? __ldg(lam + sg[q]) : zero;   // mode index = grid index
+  }
+  if constexpr (TOEP) {
+    const TACCI* accin = reinterpret_cast<const TACCI*>(p.acc_in);
+    const R* Dr = reinterpret_cast<const R*>(p.Dr);
+#pragma unroll
+    for (int q = 0; q < QN; ++q) {
+      aq[q] = (accin && sok[q]) ? to_c<R>(__ldg(accin + sg[q])) : zero;
+      if constexpr ((FLAGS & F_TOEP_X) != 0) dq[q] = (Dr && sok[q]) ? __ldg(Dr + sg[q]) : 0.f;
+    }
+  }
+
+  // ---- tile and twiddles into shared memory ------------------------------------------------------
+#pragma unroll
+  for (int q = 0; q < QL; ++q) {
+    const int i = tid + q * nthr;
+    if (i < L - 1) tws[i] = twr[q];
+  }
+#pragma unroll
+  for (int q = 0; q < QN; ++q) {
+    if (!sin_[q]) continue;
+    at(sl[q], 1 + sp[q]) = xq[q];
+    if constexpr ((FLAGS & F_DST) != 0) at(sl[q], L - 1 - sp[q]) = cneg(xq[q]);   // odd extension
+  }
+  for (int l = tid; l < B; l += nthr) {
+    at(l, 0) = zero;
+    at(l, Nh) = zero;
+  }
+  if constexpr ((FLAGS & F_DST) == 0) {  // zero padding of the circulant embedding
+#pragma unroll
+    for (int q = 0; q < QN; ++q) {
+      const int e = tid + q * nthr;
+      if (e < B * (Nh - 1)) {
+        const int l = e / (Nh - 1);
+        at(l, Nh + 1 + (e - l * (Nh - 1))) = zero;
+      }
+    }
+  }
+  __syncthreads();
+  const R dsc = p.dst_scale_f;
+
+  // ---- sine transforms ------------------------------------------------------------------------
+  if constexpr ((FLAGS & F_DST) != 0) {
+    fft_lines_fixed<LOG2L, kFixedLogR, false, false, false>(buf, Lp, B, tws);
+    if constexpr ((FLAGS & F_LAM) != 0) {
+#pragma unroll
+      for (int q = 0; q < QN; ++q) {
+        if (!sin_[q]) continue;
+        const int k = sp[q] + 1;  // sine mode k = 1..n along this axis
+        at(sl[q], k) = cmul(at(sl[q], k), lq[q]);
+        at(sl[q], L - k) = cmul(at(sl[q], L - k), lq[q]);
+      }
+      for (int l = tid; l < B; l += nthr) {
+        at(l, 0) = zero;
+        at(l, Nh) = zero;
+      }
+      __syncthreads();
+      fft_lines_fixed<LOG2L, kFixedLogR, false, false, false>(buf, Lp, B, tws);
+    }
+  }
+
+  // ---- DST output / D sub-solve ---------------------------------------------------------------
+  V zq[QN];
+#pragma unroll
+  for (int q = 0; q < QN; ++q) zq[q] = xq[q];
+  if constexpr ((FLAGS & F_DST) != 0 && (FLAGS & F_DSCALE) == 0) {
+    TOUT* out = reinterpret_cast<TOUT*>(p.out);
+#pragma unroll
+    for (int q = 0; q < QN; ++q)
+      if (sok[q]) st_c(out + sg[q], cmul_i(cscale(at(sl[q], 1 + sp[q]), dsc)));
+  }
+  if constexpr ((FLAGS & F_DSCALE) != 0) {
+#pragma unroll
+    for (int q = 0; q < QN; ++q) {
+      V z = zero;
+      if (sok[q]) {
+        z = xq[q];  // identity preconditioner: the input
+        if constexpr ((FLAGS & F_DST) != 0) z = cmul_i(cscale(at(sl[q], 1 + sp[q]), dsc));
+        z = cmul(z, fq[q]);
+        if (zout) st_c(zout + sg[q], p.z_add ? cadd(oq[q], z) : z);
+      }
+      zq[q] = z;
+      if constexpr (TOEP) {
+        if (sin_[q]) at(sl[q], 1 + sp[q]) = z;
+      }
+    }
+    if constexpr (TOEP) {
+#pragma unroll
+      for (int q = 0; q < QN; ++q) {
+        const int e = tid + q * nthr;
+        if (e < B * (Nh - 1)) {
+          const int l = e / (Nh - 1);
+          at(l, Nh + 1 + (e - l * (Nh - 1))) = zero;
+        }
+      }
+      for (int l = tid; l < B; l += nthr) {
+        at(l, 0) = zero;
+        at(l, Nh) = zero;
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- Toeplitz product by circulant embedding ------------------------------------------------
+  if constexpr (TOEP) {
+    fft_lines_fixed<LOG2L, kFixedLogR, false, true, false>(buf, Lp, B, tws);   // zero upper half in
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+      const int e = tid + q * nthr;
+      V& v = at(e >> LOG2L, e & (L - 1));
+      v = cscale(v, cq[q]);
+    }
+    __syncthreads();
+    fft_lines_fixed<LOG2L, kFixedLogR, true, false, true>(buf, Lp, B, tws);    // lower half out
+    const V ca = p.ca_f, cb = p.cb_f;
+    TACCO* accout = reinterpret_cast<TACCO*>(p.acc_out);
+#pragma unroll
+    for (int q = 0; q < QN; ++q) {
+      if (!sok[q]) continue;
+      V t = at(sl[q], 1 + sp[q]);
+      V acc = aq[q];
+      if constexpr ((FLAGS & F_TOEP_X) != 0) {
+        t = csub(t, cscale(zq[q], dq[q]));
+        acc = cadd(acc, cmul(ca, zq[q]));
+      }
+      acc = cadd(acc, cmul(cb, t));
+      st_c(accout + sg[q], acc);
+    }
+  }
+}
+
 // Threads per line (one or two radix-4 butterflies each) and lines per block for FFT length L.
 inline void pass_geometry(int L, bool xax, long long lines_avail, int& nt, int& B) {
   nt = L / 4;
@@ -416,7 +681,19 @@ inline void pass_geometry_fixed(int L, bool xax, long long lines_avail, long lon
 template <typename R, typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS>
 struct PassKernels {
   using Fn = void (*)(const PassParams);
-  static Fn get(int log2L) {
+  // prefetch: the fixed-length FP32 passes run k_line_pass_fixed (not for the Bluestein passes)
+  static Fn get(int log2L, bool prefetch) {
+    if constexpr (sizeof(R) == 4 && (FLAGS & F_CIRC) == 0) {
+      if (prefetch) {
+        switch (log2L) {
+          case 8: return k_line_pass_fixed<TIN, TOUT, TACCI, TACCO, FLAGS, 8>;
+          case 9: return k_line_pass_fixed<TIN, TOUT, TACCI, TACCO, FLAGS, 9>;
+          case 10: return k_line_pass_fixed<TIN, TOUT, TACCI, TACCO, FLAGS, 10>;
+          case 11: return k_line_pass_fixed<TIN, TOUT, TACCI, TACCO, FLAGS, 11>;
+          default: break;
+        }
+      }
+    }
     if constexpr (sizeof(R) == 4) {
       switch (log2L) {
         case 8: return k_line_pass<R, TIN, TOUT, TACCI, TACCO, FLAGS, 8>;
@@ -433,8 +710,11 @@ struct PassKernels {
     cudaError_t e = cudaSuccess;
     for (int lg = 0; lg <= 12; ++lg) {
       if (lg != 0 && !(sizeof(R) == 4 && fixed_fft_length(lg))) continue;
-      const cudaError_t r = cudaFuncSetAttribute(get(lg), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      if (e == cudaSuccess) e = r;
+      for (int pf = 0; pf < 2; ++pf) {
+        const cudaError_t r = cudaFuncSetAttribute(get(lg, pf != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   200 * 1024);
+        if (e == cudaSuccess) e = r;
+      }
     }
     return e;
   }
@@ -480,10 +760,18 @@ cudaError_t launch_pass(rfnse_ctx* c, PassParams p, cudaStream_t s) {
     const long long nhi = p.nlines / p.stride;
     grid = p.tiles_inner * nhi;
   }
-  size_t smem = ((size_t)p.B * fft_line_stride(p.L) + (fixed ? 0 : p.L)) * sizeof(V);
-  if (FLAGS & F_TOEP_X) smem += (size_t)p.B * p.n * sizeof(V);
+  // tile; twiddles staged in shared memory (all but the fixed-length Bluestein passes, which read
+  // them through L1); z of the x-Toeplitz pass saved in shared memory (k_line_pass only)
+  // grids of up to about four waves wait on latency: the prefetching kernel (k_line_pass_fixed, ~105
+  // registers) is faster there; larger grids keep k_line_pass and its higher occupancy (2-D 511^2:
+  // fused x-pass 18.0 -> 15.2 us; 3-D 255^3: equal or slightly slower with the prefetching kernel)
+  const long long grid_est = xax ? (p.nlines + p.B - 1) / p.B : ((p.stride + p.B - 1) / p.B) * (p.nlines / p.stride);
+  const bool prefetch = grid_est <= 4 * 152;
+  const bool regz = fixed && !(FLAGS & F_CIRC) && prefetch;
+  size_t smem = ((size_t)p.B * fft_line_stride(p.L) + ((fixed && !regz) ? 0 : p.L)) * sizeof(V);
+  if ((FLAGS & F_TOEP_X) && !regz) smem += (size_t)p.B * p.n * sizeof(V);
   using K = PassKernels<R, TIN, TOUT, TACCI, TACCO, FLAGS>;
-  const auto kern = K::get(fixed ? p.log2L : 0);
+  const auto kern = K::get(fixed ? p.log2L : 0, prefetch);
   static const cudaError_t attr_err = K::allow_smem();
   if (attr_err != cudaSuccess) return attr_err;
   if (grid <= 0) return cudaSuccess;
