@@ -84,16 +84,13 @@ __global__ void __launch_bounds__(kCtlThreads) k_mgs_step(GmresState* gs, const 
       double2 wv = w[k];
       if (vp) {
         const double2 pv = vp[k];
-        wv.x -= hprev * pv.x;
-        wv.y -= hprev * pv.y;
+        wv.x = fma(-hprev, pv.x, wv.x);
+        wv.y = fma(-hprev, pv.y, wv.y);
         w[k] = wv;
       }
-      if (vi) {
-        const double2 a = vi[k];
-        acc += a.x * wv.x + a.y * wv.y;
-      } else {
-        acc += wv.x * wv.x + wv.y * wv.y;
-      }
+      const double2 a = vi ? vi[k] : wv;  // FMA chains: GB300 issues 2 FP64 FMAs per SM and cycle
+      acc = fma(a.x, wv.x, acc);
+      acc = fma(a.y, wv.y, acc);
     }
     acc = block_sum_c(acc, sh);
     if (threadIdx.x == 0) buf[blockIdx.x] = acc;
