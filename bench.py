@@ -58,8 +58,9 @@ def measured_hbm_gbs():
         return 6800.0, "fallback"
 
 
-# DRAM read+write per launch of the FP32 fused DST-x + (wI+D) + Toeplitz-x pass (ncu, 2-D 511^2)
-TRAFFIC_FP32_FUSED_X = {"2d": 5286656 + 0}
+# DRAM read+write per launch of the FP32 fused DST-x + (wI+D) + Toeplitz-x pass (ncu, 2-D 511^2,
+# k_line_pass_fixed<float2, float2, double2, float2, 26, 10>)
+TRAFFIC_FP32_FUSED_X = {"2d": 5288960 + 0}
 # DRAM read+write per launch of the double-float residual x-pass (ncu, 2-D 511^2, steady launch)
 TRAFFIC_DF_TOEP_X = {"2d": 6368768 + 0}
 
