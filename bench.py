@@ -61,6 +61,9 @@ def measured_hbm_gbs():
 # DRAM read+write per launch of the FP32 fused DST-x + (wI+D) + Toeplitz-x pass (ncu, 2-D 511^2,
 # k_line_pass_fixed<float2, float2, double2, float2, 26, 10>)
 TRAFFIC_FP32_FUSED_X = {"2d": 5288960 + 0}
+# DRAM read+write per launch of the cooperative Arnoldi kernel (ncu, 2-D 511^2: mean of 8 consecutive
+# launches, columns j = 1,0,1,2,0,1,0,1, the mix of the bench's solves; (j + 2) x 4.2 MB each)
+TRAFFIC_ARNOLDI = {"2d": 11536928 + 0}
 # DRAM read+write per launch of the double-float residual x-pass (ncu, 2-D 511^2, steady launch)
 TRAFFIC_DF_TOEP_X = {"2d": 6368768 + 0}
 
@@ -80,15 +83,23 @@ def parse():
                     help="drive the GMRES loops from the host (no CUDA graphs; same kernels, for kernel profilers)")
     ap.add_argument("--alu-probe", action="store_true",
                     help="only measure the FP64 and FP32 FMA rates of the GPU and print them")
+    ap.add_argument("--arnoldi-probe", action="store_true",
+                    help="only time the cooperative Arnoldi kernel (MGS + Givens) per column j on the 2-D and "
+                         "3-D grid sizes and print the times")
+    ap.add_argument("--instances", type=int, default=3,
+                    help="2d workload: number of 511^2 instances advanced together (alphas cycle through "
+                         "1.2, 1.5, 1.9); the default 3 is the headline configuration")
     return ap.parse_args()
 
 
-def workload(name):
+def workload(name, instances=3):
     """[(problem, u0)] and a description."""
     if name == "2d":
-        inst = [W.config_2d(a)[:2] for a in W.CONFIG_2D_ALPHAS]
-        desc = {"workload": "2d_n511x511_alpha{1.2,1.5,1.9}_rho2_dt0.005_tol1e-10", "d": 2, "n": [511, 511],
-                "box": [-10, 10], "alphas": list(W.CONFIG_2D_ALPHAS), "instances": 3}
+        alphas = [W.CONFIG_2D_ALPHAS[i % len(W.CONFIG_2D_ALPHAS)] for i in range(instances)]
+        inst = [W.config_2d(a)[:2] for a in alphas]
+        tag = "" if instances == 3 else f"_x{instances}"
+        desc = {"workload": "2d_n511x511_alpha{1.2,1.5,1.9}_rho2_dt0.005_tol1e-10" + tag, "d": 2, "n": [511, 511],
+                "box": [-10, 10], "alphas": alphas, "instances": instances}
     elif name == "3d":
         p, u0, _ = W.config_3d()
         inst = [(p, u0)]
@@ -228,7 +239,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    inst, desc = workload(args.workload)
+    inst, desc = workload(args.workload, args.instances)
     from oracle.scheme import SchemeOracle
     # one bench step = one time step of one instance (instances visited in turn), CPU oracle
     states = []
@@ -278,7 +289,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
     from paper_2410_03643_gb300 import build, rfnse
     build.build_library()
-    inst, desc = workload(args.workload)
+    inst, desc = workload(args.workload, args.instances)
     main = torch.cuda.current_stream()
     concurrent = not args.serial and len(inst) > 1
     pool = ThreadPoolExecutor(max_workers=len(inst)) if concurrent else None
@@ -401,6 +412,13 @@ def run_ours(args):
         ms_r32, _, _, _, prof32 = timed(prof_solvers, nprof, args.warmup, profile_kind=k32, serial=True)
         for s in prof_solvers:
             s.close()
+    # the cooperative Arnoldi kernel (MGS, Givens, test), launched on its own by the host-driven loops
+    prof_arn = None
+    if args.workload in ("2d", "3d"):
+        prof_solvers = make(1, device_loop=0, batch=False)
+        ms_ra, _, _, _, prof_arn = timed(prof_solvers, nprof, args.warmup, profile_kind=rfnse.K_ARNOLDI, serial=True)
+        for s in prof_solvers:
+            s.close()
     ms_max = reduce_max(ms, world, dev)
     value = weak_value(world, dof_per_step, args.steps, ms_max)
 
@@ -455,7 +473,8 @@ def run_ours(args):
         n, pms, fl, by = prof32
         hbm, how = measured_hbm_gbs()
         achieved = by / (pms * 1e-3) / 1e9
-        entries.append({"bound": "hbm", "kernel": "k_line_pass<float,F_DST|F_DSCALE|F_TOEP_X> "
+        entries.append({"bound": "hbm", "kernel": ("k_line_pass_fixed" if args.workload == "2d" else "k_line_pass")
+                                                  + "<float,F_DST|F_DSCALE|F_TOEP_X> "
                                                   "(FP32 inverse DST x + (wI+D) + Toeplitz x)",
                         "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                         # profiles/k_line_pass_fp32_fused_x_2d511.md
@@ -467,11 +486,31 @@ def run_ours(args):
                         "frac_of_fp32_alu_peak": fl / (pms * 1e-3) / FP32_ALU_PEAK_FLOPS,
                         "peak_note": f"copy bandwidth, {how} (MEASURED_PEAKS.json); arithmetic intensity "
                                      f"{fl / by:.1f} flop/B is below the FP32 balance point"})
+    if prof_arn and prof_arn[0] > 0:
+        n, pms, fl, by = prof_arn
+        hbm, how = measured_hbm_gbs()
+        achieved = fl / (pms * 1e-3) / 1e12
+        entries.append({"bound": "alu", "kernel": "k_mgs_step (cooperative MGS + Givens + convergence test, "
+                                                  "one launch per Arnoldi step)",
+                        "achieved": achieved, "peak": FP64_ALU_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                        "frac": achieved * 1e12 / FP64_ALU_PEAK_FLOPS,
+                        # profiles/k_mgs_step_2d511.md
+                        "traffic": TRAFFIC_ARNOLDI.get(args.workload), "launches": n,
+                        "avg_launch_us": 1e3 * pms / n, "total_ms": pms,
+                        "share_of_step_time": pms / ms_ra if ms_ra > 0 else None, "measured": measured,
+                        "algorithmic_flops_per_launch": fl / n, "algorithmic_bytes_per_launch": by / n,
+                        "achieved_GBs": by / (pms * 1e-3) / 1e9, "frac_of_hbm": by / (pms * 1e-3) / 1e9 / hbm,
+                        "peak_note": "FP64 FMA issue rate, 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz (1.26 TFLOP/s "
+                                     "measured by --alu-probe); the kernel performs j + 2 sweeps with a grid-wide "
+                                     "reduction after each, and the synchronisation between sweeps, not the FP64 "
+                                     f"pipe or memory, sets its time ({how} copy bandwidth beside it)"})
     if entries:
         entries.sort(key=lambda e: -e["total_ms"])
         out["roofline"] = entries[0]
         if len(entries) > 1:
             out["roofline_second"] = entries[1]
+        if len(entries) > 2:
+            out["roofline_third"] = entries[2]
     if clk:
         out["clocks"] = clk
 
@@ -779,6 +818,22 @@ def run_omega(args):
     print(json.dumps(out), flush=True)
 
 
+def arnoldi_probe():
+    """Duration of the cooperative Arnoldi kernel per column j (CUDA events, 20 launches each)."""
+    import torch
+    from paper_2410_03643_gb300 import build, rfnse
+    build.build_library()
+    props = torch.cuda.get_device_properties(0)
+    out = {"device": props.name, "what": "k_mgs_step: MGS against j+1 basis vectors, Givens, test"}
+    for name, n in (("2d_511^2", 511 * 511), ("3d_255^3", 255 ** 3)):
+        rows = {}
+        for j in (0, 1, 2, 3, 4, 7):
+            us, blocks = rfnse.probe_arnoldi(n, j)
+            rows[str(j)] = round(us, 2)
+        out[name] = {"n": n, "blocks": blocks, "us_per_step_by_j": rows}
+    print(json.dumps(out), flush=True)
+
+
 def alu_probe():
     import torch
     from paper_2410_03643_gb300 import build, rfnse
@@ -794,6 +849,9 @@ def main():
     args = parse()
     if args.alu_probe:
         alu_probe()
+        return
+    if args.arnoldi_probe:
+        arnoldi_probe()
         return
     if args.impl == "reference":
         run_reference(args)

@@ -258,10 +258,22 @@ long long rfnse_launch_count(void);
    the FP64 arithmetic peak that bounds the FP64 line passes.  Errors: EINVAL, ENOMEM, ECUDA. */
 int rfnse_probe_fma(int fp64, double* flops_per_s);
 
+/* Time the cooperative Arnoldi kernel alone: one step of modified Gram-Schmidt against j + 1 basis
+   vectors of n complex FP64 values, the Givens update and the convergence test (paper Sec. 5, the
+   orthogonalisation inside PGMRES), on synthetic vectors, with the grid the solver uses for n.
+   *us_per_step (host) receives the mean CUDA-event duration of `reps` launches after two untimed
+   ones; *blocks_out (host, may be NULL) the grid size.  Allocates (j + 2) n complex values on the
+   device and frees them before returning.  0 <= j <= 62, 1 <= n <= 2^28, 1 <= reps <= 1000.
+   Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT (a bounded grid-barrier wait gave up). */
+int rfnse_probe_arnoldi(long long n, int j, int reps, double* us_per_step, int* blocks_out);
+
 /* Kernel classes of rfnse_profile: OR of the operations a line pass fuses, plus RFNSE_K_FP32 for
    passes computing in FP32 and RFNSE_K_DF for the Toeplitz passes of the mixed form's residual, which
    compute their FFTs in double-float (pairs of FP32 numbers, about 48 significant bits) when every
-   axis has n + 1 in {128, 256, 512, 1024}.  RFNSE_K_INSCALE is ignored when matching. */
+   axis has n + 1 in {128, 256, 512, 1024}.  RFNSE_K_INSCALE is ignored when matching.
+   RFNSE_K_ARNOLDI alone selects the cooperative Arnoldi kernel (modified Gram-Schmidt against j + 1
+   basis vectors, Givens, convergence test) as launched by the host-driven loops (device_loop = 0);
+   its algorithmic figures per launch are 8 (j + 1) + 4 flops and 16 (j + 3) bytes per grid point. */
 enum {
   RFNSE_K_INSCALE = 1,   /* Arnoldi normalisation v = w / h folded into the load */
   RFNSE_K_DST = 2,       /* DST-I along the axis */
@@ -270,7 +282,8 @@ enum {
   RFNSE_K_TOEP_X = 16,   /* Toeplitz product along x with the diagonal and block coupling */
   RFNSE_K_TOEP_ACC = 32, /* Toeplitz product along y or z, accumulated */
   RFNSE_K_FP32 = 256,
-  RFNSE_K_DF = 1024
+  RFNSE_K_DF = 1024,
+  RFNSE_K_ARNOLDI = 2048
 };
 
 /* Start timing every launch of kernel class `kind` (0 = off) issued by ctx: a CUDA event pair is

@@ -106,10 +106,6 @@ inline int choose_reduce_blocks(long long N) {
 // ---- Krylov / pointwise kernels (krylov.cu) -----------------------------------------------------
 // All reductions are deterministic: fixed grid, per-block partials, the last block to finish sums
 // the partials in block order.
-void launch_dot_axpy(const double2* vi, double2* w, const double2* vprev, const double* hprev, double* out,
-                     long long N, int blocks, double* partials, unsigned* counter, cudaStream_t s);
-void launch_norm_givens(const double2* vj, double2* w, const double* hjj, GmresState* gs, int j, long long N,
-                        int blocks, double* partials, unsigned* counter, cudaStream_t s);
 void launch_norm(const double2* x, GmresState* gs, long long N, int blocks, double* partials, unsigned* counter,
                  cudaStream_t s);
 void launch_backsolve(GmresState* gs, int k, cudaStream_t s);

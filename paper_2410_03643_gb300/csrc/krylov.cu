@@ -1,6 +1,8 @@
-// Arnoldi (modified Gram-Schmidt), Givens and pointwise kernels of the GMRES solve (paper Sec. 5,
-// "PGMRES").  Krylov vectors are complex FP64 with the real inner product <a, b> = Re(a^H b), which
-// is the Euclidean inner product of the real block vectors [Im; Re] of Sec. 3.
+// Norms, cycle start, back-substitution, solution updates and pointwise kernels of the GMRES solve
+// (paper Sec. 5, "PGMRES") as the host-driven loops use them; the Arnoldi step itself (modified
+// Gram-Schmidt, Givens) is the cooperative kernel of control.cu in both loop forms.  Krylov vectors
+// are complex FP64 with the real inner product <a, b> = Re(a^H b), which is the Euclidean inner
+// product of the real block vectors [Im; Re] of Sec. 3.
 #include <cmath>
 #include "internal.cuh"
 #include "cplx.cuh"
@@ -46,80 +48,6 @@ __device__ __forceinline__ double final_sum(const double* partials, unsigned* co
   return v;
 }
 
-// w -= (*hprev) vprev (if vprev), then out = <vi, w>.
-__global__ void __launch_bounds__(kRedThreads) k_dot_axpy(const double2* __restrict__ vi, double2* __restrict__ w,
-                                                          const double2* __restrict__ vprev,
-                                                          const double* hprev, double* out, long long N,
-                                                          double* partials, unsigned* counter) {
-  __shared__ double sh[32];
-  const double h = vprev ? *hprev : 0.0;
-  double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    double2 wv = w[i];
-    if (vprev) {
-      const double2 pv = vprev[i];
-      wv.x -= h * pv.x;
-      wv.y -= h * pv.y;
-      w[i] = wv;
-    }
-    const double2 a = vi[i];
-    acc += a.x * wv.x + a.y * wv.y;
-  }
-  const double part = block_sum(acc, sh);
-  if (arrive_last(part, partials, counter)) {
-    const double s = final_sum(partials, counter, sh);
-    if (threadIdx.x == 0) *out = s;
-  }
-}
-
-// w -= h_jj v_j; h_{j+1,j} = ||w||; Givens update of column j; convergence test.
-__global__ void __launch_bounds__(kRedThreads) k_norm_givens(const double2* __restrict__ vj, double2* __restrict__ w,
-                                                             const double* hjj, GmresState* gs, int j, long long N,
-                                                             double* partials, unsigned* counter) {
-  __shared__ double sh[32];
-  const double h = *hjj;
-  double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    double2 wv = w[i];
-    const double2 pv = vj[i];
-    wv.x -= h * pv.x;
-    wv.y -= h * pv.y;
-    w[i] = wv;
-    acc += wv.x * wv.x + wv.y * wv.y;
-  }
-  const double part = block_sum(acc, sh);
-  if (arrive_last(part, partials, counter)) {
-    const double s = final_sum(partials, counter, sh);
-    if (threadIdx.x == 0) {
-      const int ld = kMaxM + 1;
-      double* Hc = gs->H + (size_t)j * ld;
-      const double hnext = sqrt(s);
-      Hc[j + 1] = hnext;
-      for (int i = 0; i < j; ++i) {  // previous rotations
-        const double t = gs->cs[i] * Hc[i] + gs->sn[i] * Hc[i + 1];
-        Hc[i + 1] = -gs->sn[i] * Hc[i] + gs->cs[i] * Hc[i + 1];
-        Hc[i] = t;
-      }
-      const double rr = hypot(Hc[j], Hc[j + 1]);
-      const double c = Hc[j] / rr, sn = Hc[j + 1] / rr;
-      gs->cs[j] = c;
-      gs->sn[j] = sn;
-      Hc[j] = rr;
-      Hc[j + 1] = 0.0;
-      gs->g[j + 1] = -sn * gs->g[j];
-      gs->g[j] = c * gs->g[j];
-      const double rel = fabs(gs->g[j + 1]) / gs->ref;
-      gs->relres = rel;
-      gs->inv_h = (hnext > 0.0) ? 1.0 / hnext : 0.0;
-      int done = 0;
-      if (!isfinite(rel) || !isfinite(hnext)) done = 3;
-      else if (rel < gs->tol) done = 1;
-      else if (hnext == 0.0) done = 2;
-      gs->done = done;
-    }
-  }
-}
-
 // beta = ||x||, 1/beta, g = beta e_1; clears the column state of a new cycle.
 __global__ void __launch_bounds__(kRedThreads) k_norm(const double2* __restrict__ x, GmresState* gs, long long N,
                                                       double* partials, unsigned* counter) {
@@ -147,6 +75,9 @@ __global__ void k_start_cycle(GmresState* gs, double ref, double tol) {
   gs->ref = (ref > 0.0) ? ref : gs->beta;
   gs->tol = tol;
   gs->relres = gs->beta / gs->ref;
+  gs->j = 0;  // the cooperative Arnoldi kernel takes the column index from the state
+  gs->it = 0;
+  gs->err = 0;
 }
 
 // y = R^{-1} g on the leading k x k triangle (single thread; k <= 64).
@@ -266,16 +197,6 @@ static inline unsigned ew_blocks(long long N) {
   return (unsigned)b;
 }
 
-void launch_dot_axpy(const double2* vi, double2* w, const double2* vprev, const double* hprev, double* out,
-                     long long N, int blocks, double* partials, unsigned* counter, cudaStream_t s) {
-  count_launch();
-  k_dot_axpy<<<blocks, kRedThreads, 0, s>>>(vi, w, vprev, hprev, out, N, partials, counter);
-}
-void launch_norm_givens(const double2* vj, double2* w, const double* hjj, GmresState* gs, int j, long long N,
-                        int blocks, double* partials, unsigned* counter, cudaStream_t s) {
-  count_launch();
-  k_norm_givens<<<blocks, kRedThreads, 0, s>>>(vj, w, hjj, gs, j, N, partials, counter);
-}
 void launch_norm(const double2* x, GmresState* gs, long long N, int blocks, double* partials, unsigned* counter,
                  cudaStream_t s) {
   count_launch();

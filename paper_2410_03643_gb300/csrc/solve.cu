@@ -104,7 +104,6 @@ cudaError_t run_apply_A(rfnse_ctx* c, const double2* u, double2* out, const doub
 }
 
 // ---------------------------------------------------------------------------------------------
-static inline double* Hp(rfnse_ctx* c, int i, int j) { return &c->gs->H[(size_t)j * (kMaxM + 1) + i]; }
 
 static rfnse_status peek(rfnse_ctx* c, GmresPeek* out) {
   RFNSE_CUDA_TRY(c, cudaMemcpyAsync(c->peek, c->gs, sizeof(GmresPeek), cudaMemcpyDeviceToHost, c->stream));
@@ -115,16 +114,45 @@ static rfnse_status peek(rfnse_ctx* c, GmresPeek* out) {
 
 // ---- host loop -------------------------------------------------------------------------------
 
-// Modified Gram-Schmidt of w against V_0..V_j, then h_{j+1,j}, Givens and the convergence test.
-static void arnoldi_orthogonalise(rfnse_ctx* c, int j) {
+static SolveCfg make_cfg(const rfnse_ctx* c, int mixed) {
+  SolveCfg cfg{};
+  cfg.m = c->p.restart;
+  cfg.max_it = c->p.max_it;
+  cfg.max_outer = mixed ? (c->p.max_outer > 0 ? c->p.max_outer : 30) : (1 << 30);
+  cfg.mixed = mixed;
+  cfg.tol = c->p.tol;
+  cfg.eta_min = c->p.inner_tol > 0 ? c->p.inner_tol : 1e-6;
+  return cfg;
+}
+
+// Modified Gram-Schmidt of w against V_0..V_j, then h_{j+1,j}, Givens and the convergence test: the
+// cooperative kernel of the device loop, launched on its own (gs->j = j).  Timed per launch under
+// rfnse_profile(RFNSE_K_ARNOLDI).
+static cudaError_t arnoldi_orthogonalise(rfnse_ctx* c, int j) {
   const long long N = c->N;
-  for (int i = 0; i <= j; ++i) {
-    launch_dot_axpy(c->V + (size_t)i * N, c->w, i > 0 ? c->V + (size_t)(i - 1) * N : nullptr,
-                    i > 0 ? Hp(c, i - 1, j) : nullptr, Hp(c, i, j), N, c->red_blocks, c->partials, c->counter,
-                    c->stream);
+  const SolveCfg cfg = make_cfg(c, c->p.precision == 1 ? 1 : 0);
+  const bool prof = c->prof_kind == RFNSE_K_ARNOLDI;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (prof) {
+    while (c->prof_used + 2 > c->prof_events.size()) {
+      cudaEvent_t ev;
+      const cudaError_t e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) return e;
+      c->prof_events.push_back(ev);
+    }
+    e0 = c->prof_events[c->prof_used];
+    e1 = c->prof_events[c->prof_used + 1];
+    c->prof_used += 2;
+    cudaEventRecord(e0, c->stream);
   }
-  launch_norm_givens(c->V + (size_t)j * N, c->w, Hp(c, j, j), c->gs, j, N, c->red_blocks, c->partials, c->counter,
-                     c->stream);
+  const cudaError_t e = launch_mgs_step(c->gs, c->V, N, c->w, N, c->coop_partials, c->bar, cfg, 0, 0,
+                                        c->coop_blocks, c->stream);
+  if (prof) {
+    cudaEventRecord(e1, c->stream);
+    c->prof_flops += (8.0 * (j + 1) + 4.0) * (double)N;  // dot and update per basis vector, the norm
+    c->prof_bytes += 16.0 * (j + 3) * (double)N;         // V_0..V_j and w read once, w written once
+  }
+  return e;
 }
 
 // Right-preconditioned GMRES(m) for R x = f, x0 = 0 (paper Sec. 5 protocol), all FP64.
@@ -158,8 +186,9 @@ static rfnse_status gmres_fp64(rfnse_ctx* c, const double* D, const double2* f, 
       RFNSE_CUDA_TRY(c, (run_precon<double, double2, double2, double2, double2, true, true>(
                             c, src, scale, c->V + (size_t)j * N, c->zb, 0, D, c->w, c->w, nullptr, kOne, kI, half,
                             c->t1, c->t2)));
-      arnoldi_orthogonalise(c, j);
+      RFNSE_CUDA_TRY(c, arnoldi_orthogonalise(c, j));
       if ((st = peek(c, &pk))) return st;
+      if (pk.err) { c->err = "a bounded device-side wait gave up"; return RFNSE_ETIMEOUT; }
       ++it;
       k = j + 1;
       rel = pk.relres;
@@ -239,8 +268,9 @@ static rfnse_status solve_mixed(rfnse_ctx* c, const double* D, const double2* f,
       RFNSE_CUDA_TRY(c, (run_precon<float, double2, float2, float2, float2, true, true>(
                             c, src, scale, c->V + (size_t)j * N, c->Z32 + (size_t)j * N, 0, D, c->w, c->wp32,
                             nullptr, kOne, kI, half, c->t1f, c->t2f)));
-      arnoldi_orthogonalise(c, j);
+      RFNSE_CUDA_TRY(c, arnoldi_orthogonalise(c, j));
       if ((st = peek(c, &pk))) return st;
+      if (pk.err) { c->err = "a bounded device-side wait gave up"; return RFNSE_ETIMEOUT; }
       ++it;
       k = j + 1;
       if (pk.done == 3) { c->err = "non-finite value in the Arnoldi process"; return RFNSE_ENUMERIC; }
@@ -275,17 +305,6 @@ static rfnse_status solve_mixed(rfnse_ctx* c, const double* D, const double2* f,
 }
 
 // ---- device loop: the solve as one CUDA graph ------------------------------------------------
-
-static SolveCfg make_cfg(const rfnse_ctx* c, int mixed) {
-  SolveCfg cfg{};
-  cfg.m = c->p.restart;
-  cfg.max_it = c->p.max_it;
-  cfg.max_outer = mixed ? (c->p.max_outer > 0 ? c->p.max_outer : 30) : (1 << 30);
-  cfg.mixed = mixed;
-  cfg.tol = c->p.tol;
-  cfg.eta_min = c->p.inner_tol > 0 ? c->p.inner_tol : 1e-6;
-  return cfg;
-}
 
 // Add a conditional WHILE node at the current capture position of stream s and make it the capture's
 // dependency; returns its body graph.

@@ -54,12 +54,12 @@ class Params(ctypes.Structure):
 EXPORTED = ("rfnse_default_params", "rfnse_create", "rfnse_destroy", "rfnse_last_error", "rfnse_size",
             "rfnse_set_state", "rfnse_get_state", "rfnse_run", "rfnse_apply_A", "rfnse_apply_prec",
             "rfnse_dst", "rfnse_toeplitz", "rfnse_solve", "rfnse_get_coefficients", "rfnse_launch_count",
-            "rfnse_profile", "rfnse_profile_read", "rfnse_probe_fma", "rfnse_batch_create",
+            "rfnse_profile", "rfnse_profile_read", "rfnse_probe_fma", "rfnse_probe_arnoldi", "rfnse_batch_create",
             "rfnse_batch_destroy", "rfnse_batch_last_error", "rfnse_batch_context", "rfnse_batch_run",
             "rfnse_tape_forward", "rfnse_tape_backward", "rfnse_adjoint_solve", "rfnse_tban_solve",
             "rfnse_selftest_bounded_wait")
 
-K_INSCALE, K_DST, K_LAM, K_DSCALE, K_TOEP_X, K_TOEP_ACC, K_FP32, K_DF = 1, 2, 4, 8, 16, 32, 256, 1024
+K_INSCALE, K_DST, K_LAM, K_DSCALE, K_TOEP_X, K_TOEP_ACC, K_FP32, K_DF, K_ARNOLDI = 1, 2, 4, 8, 16, 32, 256, 1024, 2048
 
 _lib = None
 
@@ -110,6 +110,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.rfnse_profile_read.restype = ip
     lib.rfnse_probe_fma.argtypes = [ip, dp]
     lib.rfnse_probe_fma.restype = ip
+    lib.rfnse_probe_arnoldi.argtypes = [ctypes.c_longlong, ip, ip, dp, ctypes.POINTER(ctypes.c_int)]
+    lib.rfnse_probe_arnoldi.restype = ip
     lib.rfnse_batch_create.argtypes = [ctypes.POINTER(Params), ip, vp, ctypes.POINTER(vp)]
     lib.rfnse_batch_create.restype = ip
     lib.rfnse_batch_destroy.argtypes = [vp]
@@ -184,6 +186,17 @@ def probe_fma(fp64: bool) -> float:
     if st != RFNSE_OK:
         raise RfnseError(st, "rfnse_probe_fma failed")
     return v.value
+
+
+def probe_arnoldi(n: int, j: int, reps: int = 20) -> Tuple[float, int]:
+    """Mean duration in microseconds of one cooperative Arnoldi step (MGS against j + 1 basis vectors
+    of n values, Givens, convergence test) and the grid size it ran with."""
+    us = ctypes.c_double()
+    blocks = ctypes.c_int()
+    st = load_library().rfnse_probe_arnoldi(int(n), int(j), int(reps), ctypes.byref(us), ctypes.byref(blocks))
+    if st != RFNSE_OK:
+        raise RfnseError(st, "rfnse_probe_arnoldi failed")
+    return us.value, blocks.value
 
 
 def _ptr(t) -> int:

@@ -339,3 +339,33 @@ def test_bounded_device_wait_gives_up_and_the_context_stays_usable():
     u, it, rr = s.solve(dev(np.zeros(p.shape)), dev(W.random_field(p.shape, 61)))
     assert rr < p.tol and it >= 1
     s.close()
+
+
+@pytest.mark.parametrize("n", (1000, 511 * 511))
+def test_arnoldi_probe_times_the_cooperative_kernel(n):
+    """The instrumentation entry point: one launch per column j, no barrier wait gives up, and the
+    time grows with the number of MGS sweeps (j + 2)."""
+    from paper_2410_03643_gb300.rfnse import probe_arnoldi
+    times = []
+    for j in (0, 3, 7):
+        us, blocks = probe_arnoldi(n, j, reps=5)
+        assert 0.0 < us < 1e5 and blocks >= 1
+        times.append(us)
+    assert times[2] > times[0]
+
+
+@pytest.mark.parametrize("precision", (0, 1))
+def test_profile_counts_the_arnoldi_kernel_in_host_loops(precision):
+    """rfnse_profile(RFNSE_K_ARNOLDI): one timed launch per Arnoldi step of a host-driven solve, with
+    the algorithmic figures of the header (8 (j + 1) + 4 flops, 16 (j + 3) bytes per point)."""
+    from paper_2410_03643_gb300 import rfnse
+    p = SMALL[2].replace(tol=1e-10)
+    s = Solver(p, precision=precision, device_loop=0)
+    D = diag_D(W.u0_sech_product(p, [1.0] * p.d), p.rho, p.dt)
+    s.profile(rfnse.K_ARNOLDI)
+    _, it, rr = s.solve(dev(D), dev(W.random_field(p.shape, 62)))
+    n, ms, fl, by = s.profile_read()
+    s.profile(0)
+    assert rr < p.tol and n == it and ms > 0.0
+    assert fl >= (8 + 4) * p.size * n and by >= 16 * 3 * p.size * n
+    s.close()

@@ -81,3 +81,12 @@ def test_create_rejects_invalid_params_without_gpu_work(libpath):
         assert st == rfnse.RFNSE_EINVAL
         assert not h.value
         assert lib.rfnse_last_error(None)
+
+
+def test_probe_arnoldi_rejects_invalid_arguments_without_gpu_work(libpath):
+    """Argument checks come before any device call."""
+    lib = rfnse.load_library()
+    us = ctypes.c_double()
+    for n, j, reps in ((0, 0, 1), (1 << 29, 0, 1), (100, -1, 1), (100, 63, 1), (100, 0, 0), (100, 0, 1001)):
+        assert lib.rfnse_probe_arnoldi(n, j, reps, ctypes.byref(us), None) == rfnse.RFNSE_EINVAL
+    assert lib.rfnse_probe_arnoldi(100, 0, 1, None, None) == rfnse.RFNSE_EINVAL
