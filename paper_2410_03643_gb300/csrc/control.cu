@@ -66,16 +66,31 @@ __device__ __forceinline__ double fixed_sum(const double* part, int n, double* s
 // h_ij = <v_i, w>, w -= h_ij v_i; one pass per i fusing the previous subtraction with the next dot),
 // h_{j+1,j} = ||w||, the Givens update of column j and the convergence test; then the state for the
 // next column (src = w, scale = 1/h_{j+1,j}, j + 1) and, if set_cond, the inner-loop condition.
+// With pre_n > 0 the product pass that wrote w has also left pre_n block partials of h_0j = <v_0, w>:
+// every block sums them in a fixed order and the first pass (and its grid-wide reduction) is skipped.
 __global__ void __launch_bounds__(kCtlThreads) k_mgs_step(GmresState* gs, const double2* __restrict__ V,
                                                          long long ldv, double2* __restrict__ w, long long N,
                                                          double* partials, GridBarrier* bar, SolveCfg cfg,
-                                                         cudaGraphConditionalHandle h_inner, int set_cond) {
+                                                         cudaGraphConditionalHandle h_inner, int set_cond,
+                                                         const double* __restrict__ pre_part, int pre_n) {
   __shared__ double sh[32];
   const int j = gs->j;
   const int nb = gridDim.x;
   double hprev = 0.0;
   double nrm2 = 0.0;
-  for (int i = 0; i <= j + 1; ++i) {
+  int i0 = 0;
+  if (pre_n > 0) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < pre_n; b += blockDim.x) v += pre_part[b];
+    v = block_sum_c(v, sh);
+    __shared__ double bc0;
+    if (threadIdx.x == 0) bc0 = v;
+    __syncthreads();
+    hprev = bc0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) gs->H[(size_t)j * (kMaxM + 1)] = hprev;
+    i0 = 1;
+  }
+  for (int i = i0; i <= j + 1; ++i) {
     double* buf = partials + (size_t)(i & 1) * nb;
     const double2* vi = (i <= j) ? V + (size_t)i * ldv : nullptr;
     const double2* vp = (i > 0) ? V + (size_t)(i - 1) * ldv : nullptr;
@@ -388,7 +403,8 @@ int coop_blocks_for(long long N) {
 
 cudaError_t launch_mgs_step(GmresState* gs, const double2* V, long long ldv, double2* w, long long N,
                             double* partials, GridBarrier* bar, const SolveCfg& cfg,
-                            cudaGraphConditionalHandle h_inner, int set_cond, int blocks, cudaStream_t s) {
+                            cudaGraphConditionalHandle h_inner, int set_cond, int blocks, cudaStream_t s,
+                            const double* pre_part, int pre_n) {
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3((unsigned)blocks);
   lc.blockDim = dim3(kCtlThreads);
@@ -399,7 +415,8 @@ cudaError_t launch_mgs_step(GmresState* gs, const double2* V, long long ldv, dou
   lc.attrs = attr;
   lc.numAttrs = 1;
   count_launch();
-  return cudaLaunchKernelEx(&lc, k_mgs_step, gs, V, ldv, w, N, partials, bar, cfg, h_inner, set_cond);
+  return cudaLaunchKernelEx(&lc, k_mgs_step, gs, V, ldv, w, N, partials, bar, cfg, h_inner, set_cond, pre_part,
+                            pre_n);
 }
 
 void launch_norm_ctl(const double2* x, GmresState* gs, long long N, int blocks, double* partials, unsigned* counter,

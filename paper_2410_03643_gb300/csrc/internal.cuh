@@ -11,6 +11,9 @@
 namespace rfnse {
 
 constexpr int kMaxM = 256;  // largest supported restart length
+// Largest grid of a last matrix-product pass that hands its <v_0, w> partials to the Arnoldi kernel
+// (every block of that kernel sums them; larger grids keep the kernel's own first sweep).
+constexpr int kDot0MaxBlocks = 4096;
 
 // Number of kernels this library has launched in the process (all contexts).
 extern std::atomic<long long> g_kernel_launches;
@@ -69,9 +72,11 @@ struct GridBarrier {
 
 // ---- device-side control (control.cu) -----------------------------------------------------------
 int coop_blocks_for(long long N);  // blocks of the cooperative Arnoldi kernel (all co-resident)
+// pre_part / pre_n: partials of h_0j = <v_0, w> written by the last product pass (pre_n = 0: none)
 cudaError_t launch_mgs_step(GmresState* gs, const double2* V, long long ldv, double2* w, long long N,
                             double* partials, GridBarrier* bar, const SolveCfg& cfg,
-                            cudaGraphConditionalHandle h_inner, int set_cond, int blocks, cudaStream_t s);
+                            cudaGraphConditionalHandle h_inner, int set_cond, int blocks, cudaStream_t s,
+                            const double* pre_part = nullptr, int pre_n = 0);
 void launch_norm_ctl(const double2* x, GmresState* gs, long long N, int blocks, double* partials, unsigned* counter,
                      GridBarrier* bar, const SolveCfg& cfg, int mode, cudaGraphConditionalHandle h_outer,
                      int set_cond, cudaStream_t s);
@@ -214,6 +219,8 @@ struct rfnse_ctx {
   rfnse::GridBarrier* bar = nullptr;
   double* coop_partials = nullptr;   // 2 * coop_blocks
   int coop_blocks = 1;
+  double* dot_part = nullptr;        // kDot0MaxBlocks partials of <v_0, w> from the last product pass
+  int dot0_blocks = 0;               // how many the last such launch wrote (0: none)
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;   // private stream that captures the loop bodies
   cudaStream_t cap_stream2 = nullptr;  // private stream that captures a stand-alone solve graph

@@ -22,6 +22,10 @@
 //              convolution of length L, i.e. two FFTs; no output scale (it is folded into lamfac).
 //   Without F_DST, F_DSCALE stores the loaded input itself (times dfac if given): the identity
 //   preconditioner of plain GMRES.
+//   F_DOT0     (with a Toeplitz flag, result stored in FP64) the block's partial sum of the real inner
+//              product <v_0, w> of the stored result w with dot_v0, written to dot_part[block]: the
+//              first modified Gram-Schmidt dot product of the Arnoldi step, so that the Arnoldi kernel
+//              starts from their fixed-order sum instead of a sweep of its own.
 //
 // With a = 1, b = i the Toeplitz passes give w = R z for the complex form R = I + i(T_d - D) of the
 // real block matrix R_d of eq. 'positiveBlockForm' (u = y + iz  <->  x = [z; y]).
@@ -47,6 +51,7 @@ enum : int {
   F_TOEP_X = 16,
   F_TOEP_ACC = 32,
   F_CIRC = 64,
+  F_DOT0 = 128,
 };
 
 struct PassParams {
@@ -87,7 +92,28 @@ struct PassParams {
   // double-float Toeplitz passes: ca and cb as codes when they are 0, +-1 or +-i (products become
   // swaps and sign changes), -1 otherwise
   int ca_code, cb_code;
+  // F_DOT0: v_0 (FP64, grid order) and the per-block partials (one per block of the launch)
+  const double2* dot_v0;
+  double* dot_part;
 };
+
+// Sum of v over the block, written by thread 0 to *out; every thread of the block must call it.  The
+// block size is a power of two (every pass tile is), at most 1024; below 32 the one warp is partial
+// and its tree starts at half its width.  Warp shuffles, then the warps in order: a fixed order.
+__device__ __forceinline__ void block_sum_store(double v, double* out) {
+  __shared__ double red[32];
+  const unsigned nt = blockDim.x;
+  const unsigned mask = nt >= 32u ? 0xffffffffu : ((1u << nt) - 1u);
+  for (int o = nt >= 32u ? 16 : (int)(nt >> 1); o > 0; o >>= 1) v += __shfl_down_sync(mask, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)((blockDim.x + 31) >> 5); ++q) t += red[q];
+    *out = t;
+  }
+}
 
 template <typename R> __device__ __forceinline__ cv<R> ld_c(const void* p, long long i);
 template <> __device__ __forceinline__ double2 ld_c<double>(const void* p, long long i) {
@@ -365,6 +391,7 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_line_pass(const PassParams 
     const TACCI* accin = reinterpret_cast<const TACCI*>(p.acc_in);
     TACCO* accout = reinterpret_cast<TACCO*>(p.acc_out);
     const R* Dr = reinterpret_cast<const R*>(p.Dr);
+    [[maybe_unused]] double dot = 0.0;
     for (int e = tid; e < B * n; e += nthr) {
       int l, pos;
       map(e, l, pos);
@@ -381,7 +408,13 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_line_pass(const PassParams 
       }
       acc = cadd(acc, cmul(cb, t));
       st_c(accout + g, acc);
+      if constexpr ((FLAGS & F_DOT0) != 0) {  // on the stored FP64 value
+        const double2 wv = make_double2((double)acc.x, (double)acc.y), v0 = p.dot_v0[g];
+        dot = fma(v0.x, wv.x, dot);
+        dot = fma(v0.y, wv.y, dot);
+      }
     }
+    if constexpr ((FLAGS & F_DOT0) != 0) block_sum_store(dot, p.dot_part + blockIdx.x);
   }
 }
 
@@ -634,6 +667,12 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_line_pass_fixed(const PassP
     fft_lines_fixed<LOG2L, kFixedLogR, true, false, true>(buf, Lp, B, tws);    // lower half out
     const V ca = p.ca_f, cb = p.cb_f;
     TACCO* accout = reinterpret_cast<TACCO*>(p.acc_out);
+    [[maybe_unused]] double2 v0q[QN];
+    if constexpr ((FLAGS & F_DOT0) != 0) {
+#pragma unroll
+      for (int q = 0; q < QN; ++q) v0q[q] = sok[q] ? __ldg(p.dot_v0 + sg[q]) : make_double2(0.0, 0.0);
+    }
+    [[maybe_unused]] double dot = 0.0;
 #pragma unroll
     for (int q = 0; q < QN; ++q) {
       if (!sok[q]) continue;
@@ -645,7 +684,12 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_line_pass_fixed(const PassP
       }
       acc = cadd(acc, cmul(cb, t));
       st_c(accout + sg[q], acc);
+      if constexpr ((FLAGS & F_DOT0) != 0) {  // on the stored FP64 value
+        dot = fma(v0q[q].x, (double)acc.x, dot);
+        dot = fma(v0q[q].y, (double)acc.y, dot);
+      }
     }
+    if constexpr ((FLAGS & F_DOT0) != 0) block_sum_store(dot, p.dot_part + blockIdx.x);
   }
 }
 
@@ -737,6 +781,10 @@ void pass_work(const PassParams& p, double& flops, double& bytes) {
   if ((FLAGS & F_DSCALE) && p.dfac) bytes += N * sizeof(cv<R>);
   if ((FLAGS & F_TOEP_X) && p.Dr) bytes += N * sizeof(R);
   if (FLAGS & (F_TOEP_X | F_TOEP_ACC)) bytes += N * sizeof(TACCO) + (p.acc_in ? N * sizeof(TACCI) : 0.0);
+  if (FLAGS & F_DOT0) {
+    bytes += N * sizeof(double2);
+    flops += 4.0 * N;
+  }
 }
 
 template <typename R, typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS>
@@ -774,12 +822,19 @@ cudaError_t launch_pass(rfnse_ctx* c, PassParams p, cudaStream_t s) {
   const auto kern = K::get(fixed ? p.log2L : 0, prefetch);
   static const cudaError_t attr_err = K::allow_smem();
   if (attr_err != cudaSuccess) return attr_err;
+  if constexpr ((FLAGS & F_DOT0) != 0) {  // too many partials for the Arnoldi kernel to sum: plain pass
+    if (grid > kDot0MaxBlocks || grid <= 0) {
+      c->dot0_blocks = 0;
+      return launch_pass<R, TIN, TOUT, TACCI, TACCO, FLAGS & ~F_DOT0>(c, p, s);
+    }
+    c->dot0_blocks = (int)grid;
+  }
   if (grid <= 0) return cudaSuccess;
   // a block above the launch bound would fail to launch (inside a stream capture that invalidates the
   // whole capture): refuse it here, before any launch
   if (p.B * p.nt > kPassMaxThreads || p.B * p.nt < 1) return cudaErrorInvalidConfiguration;
   const int kind = FLAGS | (sizeof(R) == 4 ? 256 : 0);
-  const bool prof = c->prof_kind != 0 && ((c->prof_kind | F_INSCALE) == (kind | F_INSCALE));
+  const bool prof = c->prof_kind != 0 && ((c->prof_kind | F_INSCALE | F_DOT0) == (kind | F_INSCALE | F_DOT0));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (prof) {
     while (c->prof_used + 2 > c->prof_events.size()) {

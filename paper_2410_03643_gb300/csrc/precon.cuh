@@ -62,6 +62,9 @@ struct Dyn {
   void* zbase = nullptr;
   long long ldv = 0;
   const int* skip = nullptr;
+  // the last product pass also leaves the block partials of <v_0, w> (v_0 = vbase) in c->dot_part
+  // for the Arnoldi kernel, and their count in c->dot0_blocks (F_DOT0)
+  bool dot0 = false;
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -92,6 +95,12 @@ cudaError_t run_precon_pc(rfnse_ctx* c, const TIN* v, const double* in_scale, do
     p.ldv = dyn.ldv;
     p.skip = dyn.skip;
   };
+  const bool dot0 = MATVEC && dyn.dot0;
+  if (MATVEC) c->dot0_blocks = 0;
+  auto with_dot0 = [&](PassParams& p) {
+    p.dot_v0 = dyn.vbase;
+    p.dot_part = c->dot_part;
+  };
   if constexpr (PC == 2) {  // no preconditioner: z = v, then the product along x
     PassParams p = base_params<R>(c, 0, h);
     p.in = v; p.in_scale = in_scale; p.copy_out = copy_v; p.out = z; p.z_add = z_add;
@@ -100,8 +109,11 @@ cudaError_t run_precon_pc(rfnse_ctx* c, const TIN* v, const double* in_scale, do
     with_dyn(p);
     if (c->d == 1) {
       p.acc_out = w;
-      if ((e = launch_pass<R, TIN, TZ, double2, double2, IS | F_DSCALE | TX>(c, p, s)) != cudaSuccess) return e;
-      return cudaSuccess;
+      if (dot0) {
+        with_dot0(p);
+        return launch_pass<R, TIN, TZ, double2, double2, IS | F_DSCALE | TX | (MATVEC ? F_DOT0 : 0)>(c, p, s);
+      }
+      return launch_pass<R, TIN, TZ, double2, double2, IS | F_DSCALE | TX>(c, p, s);
     }
     p.acc_out = wtmp;
     if ((e = launch_pass<R, TIN, TZ, double2, TW, IS | F_DSCALE | TX>(c, p, s)) != cudaSuccess) return e;
@@ -112,6 +124,11 @@ cudaError_t run_precon_pc(rfnse_ctx* c, const TIN* v, const double* in_scale, do
       p.Dr = Tables<R>::Dr(c, D); p.dfac = Tables<R>::dfac(c); p.lamfac = Tables<R>::lamfac(c, h);
       p.acc_in = w_add; p.acc_out = w; p.ca = a; p.cb = b;
       with_dyn(p);
+      if (dot0) {
+        with_dot0(p);
+        return launch_pass<R, TIN, TZ, double2, double2,
+                           IS | F_DST | CF | F_LAM | F_DSCALE | TX | (MATVEC ? F_DOT0 : 0)>(c, p, s);
+      }
       return launch_pass<R, TIN, TZ, double2, double2, IS | F_DST | CF | F_LAM | F_DSCALE | TX>(c, p, s);
     }
     {  // first axis: forward DST (and the Arnoldi normalisation)
@@ -158,7 +175,12 @@ cudaError_t run_precon_pc(rfnse_ctx* c, const TIN* v, const double* in_scale, do
       p.in_dyn_z = (dyn.gs && dyn.zbase) ? 1 : 0;
       if (a2 == c->d - 1) {
         p.acc_out = w;
-        e = launch_pass<R, TZ, TZ, TW, double2, F_TOEP_ACC>(c, p, s);
+        if (dot0) {
+          with_dot0(p);
+          e = launch_pass<R, TZ, TZ, TW, double2, F_TOEP_ACC | F_DOT0>(c, p, s);
+        } else {
+          e = launch_pass<R, TZ, TZ, TW, double2, F_TOEP_ACC>(c, p, s);
+        }
       } else {
         p.acc_out = wtmp;
         e = launch_pass<R, TZ, TZ, TW, TW, F_TOEP_ACC>(c, p, s);

@@ -125,6 +125,15 @@ static SolveCfg make_cfg(const rfnse_ctx* c, int mixed) {
   return cfg;
 }
 
+// Host-driven Arnoldi steps: operands from the host, but the last product pass leaves the partials of
+// <v_0, w> for the Arnoldi kernel as in the device loop.
+static Dyn dot0_dyn(rfnse_ctx* c) {
+  Dyn d;
+  d.vbase = c->V;
+  d.dot0 = true;
+  return d;
+}
+
 // Modified Gram-Schmidt of w against V_0..V_j, then h_{j+1,j}, Givens and the convergence test: the
 // cooperative kernel of the device loop, launched on its own (gs->j = j).  Timed per launch under
 // rfnse_profile(RFNSE_K_ARNOLDI).
@@ -146,7 +155,7 @@ static cudaError_t arnoldi_orthogonalise(rfnse_ctx* c, int j) {
     cudaEventRecord(e0, c->stream);
   }
   const cudaError_t e = launch_mgs_step(c->gs, c->V, N, c->w, N, c->coop_partials, c->bar, cfg, 0, 0,
-                                        c->coop_blocks, c->stream);
+                                        c->coop_blocks, c->stream, c->dot_part, c->dot0_blocks);
   if (prof) {
     cudaEventRecord(e1, c->stream);
     c->prof_flops += (8.0 * (j + 1) + 4.0) * (double)N;  // dot and update per basis vector, the norm
@@ -159,6 +168,7 @@ static cudaError_t arnoldi_orthogonalise(rfnse_ctx* c, int j) {
 static rfnse_status gmres_fp64(rfnse_ctx* c, const double* D, const double2* f, double2* x, int half, int* iters,
                                double* relres) {
   const long long N = c->N;
+  const Dyn dot0 = dot0_dyn(c);
   const int m = c->p.restart;
   const double tol = c->p.tol;
   GmresPeek pk;
@@ -185,7 +195,7 @@ static rfnse_status gmres_fp64(rfnse_ctx* c, const double* D, const double2* f, 
     for (int j = 0; j < m; ++j) {
       RFNSE_CUDA_TRY(c, (run_precon<double, double2, double2, double2, double2, true, true>(
                             c, src, scale, c->V + (size_t)j * N, c->zb, 0, D, c->w, c->w, nullptr, kOne, kI, half,
-                            c->t1, c->t2)));
+                            c->t1, c->t2, dot0)));
       RFNSE_CUDA_TRY(c, arnoldi_orthogonalise(c, j));
       if ((st = peek(c, &pk))) return st;
       if (pk.err) { c->err = "a bounded device-side wait gave up"; return RFNSE_ETIMEOUT; }
@@ -230,6 +240,7 @@ static rfnse_status gmres_fp64(rfnse_ctx* c, const double* D, const double2* f, 
 static rfnse_status solve_mixed(rfnse_ctx* c, const double* D, const double2* f, double2* x, int half, int* iters,
                                 double* relres, int* outer_out) {
   const long long N = c->N;
+  const Dyn dot0 = dot0_dyn(c);
   const int m = c->p.restart;
   const double tol = c->p.tol;
   const double eta_min = c->p.inner_tol > 0 ? c->p.inner_tol : 1e-6;
@@ -267,7 +278,7 @@ static rfnse_status solve_mixed(rfnse_ctx* c, const double* D, const double2* f,
     for (int j = 0; j < m && it < c->p.max_it; ++j) {
       RFNSE_CUDA_TRY(c, (run_precon<float, double2, float2, float2, float2, true, true>(
                             c, src, scale, c->V + (size_t)j * N, c->Z32 + (size_t)j * N, 0, D, c->w, c->wp32,
-                            nullptr, kOne, kI, half, c->t1f, c->t2f)));
+                            nullptr, kOne, kI, half, c->t1f, c->t2f, dot0)));
       RFNSE_CUDA_TRY(c, arnoldi_orthogonalise(c, j));
       if ((st = peek(c, &pk))) return st;
       if (pk.err) { c->err = "a bounded device-side wait gave up"; return RFNSE_ETIMEOUT; }
@@ -337,6 +348,7 @@ static cudaError_t arnoldi_step_dev(rfnse_ctx* c, int half, const SolveCfg& cfg,
   dyn.gs = c->gs;
   dyn.vbase = c->V;
   dyn.ldv = N;
+  dyn.dot0 = true;
   if (cfg.mixed) {
     dyn.zbase = c->Z32;
     e = run_precon<float, double2, float2, float2, float2, true, true>(
@@ -347,7 +359,7 @@ static cudaError_t arnoldi_step_dev(rfnse_ctx* c, int half, const SolveCfg& cfg,
   }
   if (e != cudaSuccess) return e;
   return launch_mgs_step(c->gs, c->V, N, c->w, N, c->coop_partials, c->bar, cfg, hi, set_cond, c->coop_blocks,
-                         c->stream);
+                         c->stream, c->dot_part, c->dot0_blocks);
 }
 
 // Record the solve of R x = f (c->f, c->x, c->D fixed) for one precision and half flag at the current
