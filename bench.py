@@ -61,9 +61,9 @@ def measured_hbm_gbs():
 # DRAM read+write per launch of the FP32 fused DST-x + (wI+D) + Toeplitz-x pass (ncu, 2-D 511^2,
 # k_line_pass_fixed<float2, float2, double2, float2, 26, 10>)
 TRAFFIC_FP32_FUSED_X = {"2d": 5288960 + 0}
-# DRAM read+write per launch of the cooperative Arnoldi kernel (ncu, 2-D 511^2, mean over the bench's
-# mix of columns); empty until captured for the current kernel
-TRAFFIC_ARNOLDI = {}
+# DRAM read+write per launch of the cooperative Arnoldi kernel (ncu, 2-D 511^2: mean of 10 consecutive
+# launches, columns j = 1,0,1,2,0,1,0,1,2,0, the mix of the bench's solves; (j + 2) x 4.2 MB each)
+TRAFFIC_ARNOLDI = {"2d": 11740262 + 0}
 # DRAM read+write per launch of the double-float residual x-pass (ncu, 2-D 511^2, steady launch)
 TRAFFIC_DF_TOEP_X = {"2d": 6368768 + 0}
 

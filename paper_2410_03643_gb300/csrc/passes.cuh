@@ -430,6 +430,7 @@ template <typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS
 __global__ void __launch_bounds__(kPassMaxThreads) k_line_pass_fixed(const PassParams p) {
   static_assert(!(FLAGS & F_CIRC), "the circulant comparator's passes run in k_line_pass");
   static_assert(LOG2L > 0, "fixed FFT length only");
+  static_assert(!(FLAGS & F_DOT0) || sizeof(TACCO) == sizeof(double2), "F_DOT0 needs an FP64 result");
   using R = float;
   using V = float2;
   using P = FixedPlan<LOG2L, kFixedLogR>;
@@ -663,15 +664,16 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_line_pass_fixed(const PassP
       V& v = at(e >> LOG2L, e & (L - 1));
       v = cscale(v, cq[q]);
     }
-    __syncthreads();
-    fft_lines_fixed<LOG2L, kFixedLogR, true, false, true>(buf, Lp, B, tws);    // lower half out
-    const V ca = p.ca_f, cb = p.cb_f;
-    TACCO* accout = reinterpret_cast<TACCO*>(p.acc_out);
+    // v_0 for the partials of <v_0, w>: loaded here so that the inverse FFT hides the wait
     [[maybe_unused]] double2 v0q[QN];
     if constexpr ((FLAGS & F_DOT0) != 0) {
 #pragma unroll
       for (int q = 0; q < QN; ++q) v0q[q] = sok[q] ? __ldg(p.dot_v0 + sg[q]) : make_double2(0.0, 0.0);
     }
+    __syncthreads();
+    fft_lines_fixed<LOG2L, kFixedLogR, true, false, true>(buf, Lp, B, tws);    // lower half out
+    const V ca = p.ca_f, cb = p.cb_f;
+    TACCO* accout = reinterpret_cast<TACCO*>(p.acc_out);
     [[maybe_unused]] double dot = 0.0;
 #pragma unroll
     for (int q = 0; q < QN; ++q) {
