@@ -1,9 +1,11 @@
 // Batched time stepping of many independent instances (different grids, alpha, rho, dt): every
 // instance keeps its own context and stream; once all instances are past their first step, one time
 // step of the whole batch is a single CUDA graph launch.  The graph holds, for every instance in its
-// own branch, the right-hand side, the solve with its device-decided loops (capture_solve), the update
-// of the cached T u (mixed form) and the rotation of the history by copies; it ends by gathering every
-// instance's statistics into pinned host memory.
+// own branch, the pointwise set-up (D, right-hand side, sub-solve tables), the solve with its
+// device-decided loops (capture_solve) writing u^{n+1} straight into the free history slot, and the
+// update of the cached T u (mixed form); it ends by gathering every instance's statistics into pinned
+// host memory.  The three history slots form a ring (u^{n-1}, u^n, u^{n+1} in slots v, v+1, v+2 mod 3),
+// so there are three graphs, one per phase v, and a step moves no data.
 #include <cstring>
 #include <new>
 #include <string>
@@ -19,8 +21,8 @@ struct rfnse_batch {
   std::vector<cudaStream_t> streams;  // one per instance (owned)
   cudaStream_t stream = nullptr;      // the caller's stream: the batch graph runs on it
   cudaStream_t cap = nullptr;         // private stream that captures the batch graph
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};  // one per ring phase
+  cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
   GmresState** d_gs = nullptr;        // device array of the instances' GMRES states
   GmresPeek* d_peeks = nullptr;
   GmresPeek* h_peeks = nullptr;       // pinned
@@ -35,8 +37,10 @@ const double2 kMinusI = {0.0, -1.0};
 
 void free_batch(rfnse_batch* b) {
   if (!b) return;
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->graph) cudaGraphDestroy(b->graph);
+  for (int v = 0; v < 3; ++v) {
+    if (b->exec[v]) cudaGraphExecDestroy(b->exec[v]);
+    if (b->graph[v]) cudaGraphDestroy(b->graph[v]);
+  }
   for (rfnse_ctx* c : b->ctx) rfnse_destroy(c);
   for (cudaStream_t s : b->streams)
     if (s) cudaStreamDestroy(s);
@@ -48,11 +52,16 @@ void free_batch(rfnse_batch* b) {
   delete b;
 }
 
-// Put the history in the canonical slots (u_prev in u[0], u_cur in u[1], each with its cached T u) so a
-// captured step can use fixed pointers.  Every copy goes into the slot that is free at that moment.
-cudaError_t normalise_history(rfnse_ctx* c) {
-  int p = c->iprev, q = c->icur, sp = 3 - p - q;
-  if (p == 0 && q == 1) return cudaSuccess;
+// The ring phase of c's history: v when u^{n-1} is in slot v and u^n in slot v + 1 (mod 3), else -1.
+int ring_phase(const rfnse_ctx* c) { return (c->icur == (c->iprev + 1) % 3) ? c->iprev : -1; }
+
+// Put the history in ring phase v (u_prev in u[v], u_cur in u[v + 1 mod 3], each with its cached
+// T u) so that the captured step of phase v can use fixed pointers.  Every copy goes into a slot that
+// is free at that moment; nothing moves when c is already in phase v.
+cudaError_t normalise_history(rfnse_ctx* c, int v) {
+  int p = c->iprev, q = c->icur;
+  const int tp = v, tq = (v + 1) % 3;
+  if (p == tp && q == tq) return cudaSuccess;
   const size_t bytes = sizeof(double2) * (size_t)c->N;
   cudaError_t e = cudaSuccess;
   auto move = [&](int from, int to) {
@@ -61,50 +70,47 @@ cudaError_t normalise_history(rfnse_ctx* c) {
       e = cudaMemcpyAsync(c->Tu[to], c->Tu[from], bytes, cudaMemcpyDeviceToDevice, c->stream);
     c->tu_valid[to] = c->tu_valid[from];
   };
-  if (q == 0) {  // u_cur sits in slot 0: move it to the free slot first
-    move(0, sp);
-    q = sp;
-    sp = 0;
+  if (p != tp) {
+    if (q == tp) {  // u_cur occupies u_prev's target: move it to the free slot first
+      const int f = 3 - p - q;
+      move(q, f);
+      q = f;
+    }
+    move(p, tp);
+    p = tp;
   }
-  if (p != 0) {  // slot 0 is free now
-    move(p, 0);
-    sp = p;
-    p = 0;
-  }
-  if (q != 1) move(q, 1);  // slot 1 is free now
-  c->iprev = 0;
-  c->icur = 1;
-  c->tu_valid[2] = false;
+  if (q != tq) move(q, tq);  // tq is the free slot now
+  c->iprev = tp;
+  c->icur = tq;
+  c->tu_valid[(v + 2) % 3] = false;
   return e;
 }
 
-// Record one steady-state time step of instance c (history in the canonical slots) on its stream,
-// which is capturing into graph g.
-cudaError_t capture_step(rfnse_ctx* c, cudaGraph_t g) {
+// Record one steady-state time step of instance c in ring phase v (u^{n-1} in slot v, u^n in slot
+// v + 1, u^{n+1} into slot v + 2) on its stream, which is capturing into graph g.
+cudaError_t capture_step(rfnse_ctx* c, cudaGraph_t g, int v) {
   const long long N = c->N;
-  const size_t bytes = sizeof(double2) * (size_t)N;
   cudaStream_t s = c->stream;
   const int mixed = c->p.precision == 1;
+  const int prev = v, cur = (v + 1) % 3, next = (v + 2) % 3;
   cudaError_t e;
-  launch_diag(c->u[1], nullptr, c->D, c->p.rho * c->p.dt, N, s);
   if (mixed) {
-    launch_rhs_from_tu(c->u[0], c->Tu[0], c->D, c->f, N, s);
-  } else if ((e = run_matvec_fp64(c, c->u[0], c->D, c->f, nullptr, kOne, kMinusI, 0, nullptr)) != cudaSuccess) {
-    return e;
+    launch_step_prep(c, c->u[cur], c->u[prev], c->Tu[prev], s);
+  } else {
+    launch_diag(c->u[cur], nullptr, c->D, c->p.rho * c->p.dt, N, s);
+    if ((e = run_matvec_fp64(c, c->u[prev], c->D, c->f, nullptr, kOne, kMinusI, 0, nullptr)) != cudaSuccess)
+      return e;
+    if ((e = prepare_D(c, c->D)) != cudaSuccess) return e;
   }
-  if ((e = prepare_D(c, c->D)) != cudaSuccess) return e;
-  if ((e = capture_solve(c, mixed, 0, g, s)) != cudaSuccess) return e;
-  if (mixed) launch_tu_from_residual_dev(c->gs, c->D, c->f, c->x, c->r, c->Tu[2], N, s);
-  if ((e = cudaMemcpyAsync(c->u[0], c->u[1], bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
-  if ((e = cudaMemcpyAsync(c->u[1], c->x, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
-  if (mixed) {
-    if ((e = cudaMemcpyAsync(c->Tu[0], c->Tu[1], bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
-    if ((e = cudaMemcpyAsync(c->Tu[1], c->Tu[2], bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  double2* const x_own = c->x;
+  c->x = c->u[next];  // the solve's kernels write the solution into the free slot
+  e = capture_solve(c, mixed, 0, g, s);
+  if (e == cudaSuccess && mixed) launch_tu_from_residual_dev(c->gs, c->D, c->f, c->x, c->r, c->Tu[next], N, s);
+  c->x = x_own;
+  return e;
 }
 
-cudaError_t build_batch_graph(rfnse_batch* b) {
+cudaError_t build_batch_graph(rfnse_batch* b, int v) {
   const long long launches_before = g_kernel_launches.load();
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaGraphCreate(&g, 0);
@@ -115,7 +121,7 @@ cudaError_t build_batch_graph(rfnse_batch* b) {
     for (int i = 0; i < b->count && e == cudaSuccess; ++i) {
       rfnse_ctx* c = b->ctx[i];
       e = cudaStreamWaitEvent(c->stream, fork, 0);
-      if (e == cudaSuccess) e = capture_step(c, g);
+      if (e == cudaSuccess) e = capture_step(c, g, v);
       if (e == cudaSuccess) e = cudaEventRecord(b->events[1 + i], c->stream);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->events[1 + i], 0);
     }
@@ -127,15 +133,15 @@ cudaError_t build_batch_graph(rfnse_batch* b) {
     const cudaError_t e2 = cudaStreamEndCapture(b->cap, &out);
     if (e == cudaSuccess) e = e2;
   }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[v], g, 0);
   g_kernel_launches.store(launches_before);
   if (e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
-    b->exec = nullptr;
+    b->exec[v] = nullptr;
     cudaGetLastError();
     return e;
   }
-  b->graph = g;
+  b->graph[v] = g;
   return cudaSuccess;
 }
 
@@ -239,8 +245,11 @@ int rfnse_batch_run(rfnse_batch* b, int nsteps, int* iters, double* relres) {
       }
       continue;
     }
+    // the ring phase of the first instance (or 0); the others are brought to it (no copies once
+    // every instance has advanced through the batch)
+    const int v = ring_phase(b->ctx[0]) >= 0 ? ring_phase(b->ctx[0]) : 0;
     for (rfnse_ctx* c : b->ctx) {
-      if (normalise_history(c) != cudaSuccess) {
+      if (normalise_history(c, v) != cudaSuccess) {
         b->err = "history normalisation failed";
         return RFNSE_ECUDA;
       }
@@ -251,15 +260,16 @@ int rfnse_batch_run(rfnse_batch* b, int nsteps, int* iters, double* relres) {
         return RFNSE_ECUDA;
       }
     }
-    if (!b->exec) {
-      const cudaError_t e = build_batch_graph(b);
+    if (!b->exec[v]) {
+      const cudaError_t e = build_batch_graph(b, v);
       if (e != cudaSuccess) {
         b->err = std::string("batch graph: ") + cudaGetErrorString(e);
         return RFNSE_ECUDA;
       }
     }
-    cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+    cudaError_t e = cudaGraphLaunch(b->exec[v], b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    count_launch(1);  // the statistics gather
     if (e != cudaSuccess) {
       b->err = std::string("batch step: ") + cudaGetErrorString(e);
       return RFNSE_ECUDA;
@@ -267,10 +277,14 @@ int rfnse_batch_run(rfnse_batch* b, int nsteps, int* iters, double* relres) {
     for (int i = 0; i < b->count; ++i) {
       rfnse_ctx* c = b->ctx[i];
       const GmresPeek& pk = b->h_peeks[i];
-      count_launch(solve_kernels(c, pk) + 2 + (c->p.precision == 1 ? 2 : c->d) + 1);
+      // set-up (mixed: one kernel; FP64: D, the product passes, the sub-solve tables), the solve,
+      // and (mixed) T u from the final residual
+      count_launch(solve_kernels(c, pk) + (c->p.precision == 1 ? 2 : 2 + c->d));
       c->step += 1;
-      c->tu_valid[0] = c->tu_valid[1] = (c->p.precision == 1);
-      c->tu_valid[2] = false;
+      c->iprev = (v + 1) % 3;
+      c->icur = (v + 2) % 3;
+      c->tu_valid[(v + 1) % 3] = c->tu_valid[(v + 2) % 3] = (c->p.precision == 1);
+      c->tu_valid[v] = false;
       if (iters) iters[(size_t)s * b->count + i] = pk.it;
       if (relres) relres[(size_t)s * b->count + i] = pk.relres;
       if (pk.err) {

@@ -131,6 +131,8 @@ void launch_rhs_from_tu(const double2* u, const double2* Tu, const double* D, do
 // D32 = D, dfac = 2w((w+1) + iD)/((w+1)^2 + D^2) in FP64 and FP32
 void launch_prep_D(const double* D, float* D32, double2* dfac64, float2* dfac32, double omega, long long N,
                    cudaStream_t s);
+// mixed form, steady step: D, f = u_prev - i (Tu_prev - D u_prev) and the prep_D tables in one sweep
+void launch_step_prep(rfnse_ctx* c, const double2* uc, const double2* up, const double2* Tup, cudaStream_t s);
 
 // ---- double-float Toeplitz passes (toep_df.cu) --------------------------------------------------
 bool toeplitz_df_available(const rfnse_ctx* c);
@@ -210,6 +212,7 @@ struct rfnse_ctx {
   double2* Tu[3] = {nullptr, nullptr, nullptr};
   bool tu_valid[3] = {false, false, false};
   bool resid_current = false;               // c->r holds f - R x for the last solve's x
+  bool tables_ready = false;                // the next solve's D tables are already built (k_step_prep)
   double* partials = nullptr;
   unsigned* counter = nullptr;
   int red_blocks = 1;

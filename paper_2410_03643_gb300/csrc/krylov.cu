@@ -185,6 +185,28 @@ __global__ void k_rhs_from_tu(const double2* __restrict__ u, const double2* __re
   }
 }
 
+// One steady step's pointwise set-up in the mixed form, with T u^{n-1} cached: D = rho dt |u^n|^2,
+// f = u^{n-1} - i (T u^{n-1} - D u^{n-1}) and the tables of k_prep_D, in one sweep (the same
+// arithmetic as k_diag, k_rhs_from_tu and k_prep_D in turn).
+__global__ void k_step_prep(const double2* __restrict__ uc, const double2* __restrict__ up,
+                            const double2* __restrict__ Tup, double* __restrict__ D, double2* __restrict__ f,
+                            float* __restrict__ D32, double2* __restrict__ dfac64, float2* __restrict__ dfac32,
+                            double rho_dt, double omega, long long N) {
+  const double w1 = omega + 1.0, two_w = 2.0 * omega;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = uc[i], uv = up[i], tv = Tup[i];
+    const double d = rho_dt * (v.x * v.x + v.y * v.y);
+    D[i] = d;
+    const double px = tv.x - d * uv.x, py = tv.y - d * uv.y;
+    f[i] = make_double2(uv.x + py, uv.y - px);
+    const double s = two_w / (w1 * w1 + d * d);
+    const double2 fac = make_double2(s * w1, s * d);
+    D32[i] = (float)d;
+    dfac64[i] = fac;
+    dfac32[i] = make_float2((float)fac.x, (float)fac.y);
+  }
+}
+
 __global__ void k_zero(double2* __restrict__ x, long long N) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
     x[i] = make_double2(0.0, 0.0);
@@ -242,6 +264,11 @@ void launch_rhs_from_tu(const double2* u, const double2* Tu, const double* D, do
                         cudaStream_t s) {
   count_launch();
   k_rhs_from_tu<<<ew_blocks(N), 256, 0, s>>>(u, Tu, D, f, N);
+}
+void launch_step_prep(rfnse_ctx* c, const double2* uc, const double2* up, const double2* Tup, cudaStream_t s) {
+  count_launch();
+  k_step_prep<<<ew_blocks(c->N), 256, 0, s>>>(uc, up, Tup, c->D, c->f, c->D32, c->dfac64, c->dfac32,
+                                              c->p.rho * c->p.dt, c->p.omega, c->N);
 }
 void launch_zero(double2* x, long long N, cudaStream_t s) { k_zero<<<ew_blocks(N), 256, 0, s>>>(x, N); }
 

@@ -462,7 +462,8 @@ static rfnse_status solve_graph(rfnse_ctx* c, const double* D, const double2* f,
   if (!c->graph_exec[mixed][h]) RFNSE_CUDA_TRY(c, build_solve_graph(c, mixed, h));
   if (D != c->D) RFNSE_CUDA_TRY(c, cudaMemcpyAsync(c->D, D, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->stream));
   if (f != c->f) RFNSE_CUDA_TRY(c, cudaMemcpyAsync(c->f, f, sizeof(double2) * N, cudaMemcpyDeviceToDevice, c->stream));
-  RFNSE_CUDA_TRY(c, prepare_D(c, c->D));
+  if (!c->tables_ready || D != c->D) RFNSE_CUDA_TRY(c, prepare_D(c, c->D));
+  c->tables_ready = false;
   RFNSE_CUDA_TRY(c, cudaGraphLaunch(c->graph_exec[mixed][h], c->stream));
   if (x != c->x) RFNSE_CUDA_TRY(c, cudaMemcpyAsync(x, c->x, sizeof(double2) * N, cudaMemcpyDeviceToDevice, c->stream));
   GmresPeek pk;
@@ -495,7 +496,8 @@ rfnse_status solve_block(rfnse_ctx* c, const double* D, const double2* f, double
   if (c->use_graphs) {
     st = solve_graph(c, D, f, x, half, iters, relres, &outer);
   } else {
-    RFNSE_CUDA_TRY(c, prepare_D(c, D));
+    if (!c->tables_ready || D != c->D) RFNSE_CUDA_TRY(c, prepare_D(c, D));
+    c->tables_ready = false;
     if (c->p.precision == 1) {
       st = solve_mixed(c, D, f, x, half, iters, relres, &outer);
     } else {
@@ -590,10 +592,11 @@ rfnse_status time_step(rfnse_ctx* c, int* iters, double* relres) {
   } else {
     const double2* up = c->u[c->iprev];
     const double2* uc = c->u[c->icur];
-    launch_diag(uc, nullptr, c->D, c->p.rho * c->p.dt, N, c->stream);
-    if (c->tu_valid[c->iprev]) {
-      launch_rhs_from_tu(up, c->Tu[c->iprev], c->D, c->f, N, c->stream);
+    if (c->tu_valid[c->iprev]) {  // mixed form: D, f and the sub-solve tables in one sweep
+      launch_step_prep(c, uc, up, c->Tu[c->iprev], c->stream);
+      c->tables_ready = true;
     } else {
+      launch_diag(uc, nullptr, c->D, c->p.rho * c->p.dt, N, c->stream);
       RFNSE_CUDA_TRY(c, run_matvec_fp64(c, up, c->D, c->f, nullptr, kOne, kMinusI, 0, nullptr));
     }
     st = solve_block(c, c->D, c->f, un, 0, &it, relres);
