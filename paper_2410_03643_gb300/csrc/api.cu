@@ -76,6 +76,7 @@ void free_ctx(rfnse_ctx* c) {
   cudaFree(c->bar);
   cudaFree(c->coop_partials);
   cudaFree(c->dot_part);
+  cudaFree(c->nrm_part);
   cudaFree(c->tape);
   cudaFree(c->adj_red);
   for (int a = 0; a < 3; ++a) {
@@ -247,6 +248,7 @@ int rfnse_create(const rfnse_params* p, void* stream, rfnse_ctx** out) {
   chk(dalloc(&c->bar, 1));
   chk(dalloc(&c->coop_partials, 2 * (size_t)c->coop_blocks));
   chk(dalloc(&c->dot_part, (size_t)kDot0MaxBlocks));
+  chk(dalloc(&c->nrm_part, 3 * (size_t)kNormPartMax));
   if (e == cudaSuccess) chk(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   if (e == cudaSuccess) chk(cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking));
   chk(dalloc(&c->partials, 1024));

@@ -94,8 +94,12 @@ cudaError_t capture_step(rfnse_ctx* c, cudaGraph_t g, int v) {
   const int mixed = c->p.precision == 1;
   const int prev = v, cur = (v + 1) % 3, next = (v + 2) % 3;
   cudaError_t e;
-  if (mixed) {
-    launch_step_prep(c, c->u[cur], c->u[prev], c->Tu[prev], s);
+  double* f_part = nullptr;
+  int f_n = 0;
+  if (mixed) {  // the set-up also leaves the partials of ||f||^2 for the solve's first norm
+    f_part = c->nrm_part;
+    f_n = step_prep_blocks(N);
+    launch_step_prep(c, c->u[cur], c->u[prev], c->Tu[prev], s, f_part);
   } else {
     launch_diag(c->u[cur], nullptr, c->D, c->p.rho * c->p.dt, N, s);
     if ((e = run_matvec_fp64(c, c->u[prev], c->D, c->f, nullptr, kOne, kMinusI, 0, nullptr)) != cudaSuccess)
@@ -104,7 +108,7 @@ cudaError_t capture_step(rfnse_ctx* c, cudaGraph_t g, int v) {
   }
   double2* const x_own = c->x;
   c->x = c->u[next];  // the solve's kernels write the solution into the free slot
-  e = capture_solve(c, mixed, 0, g, s);
+  e = capture_solve(c, mixed, 0, g, s, f_part, f_n);
   if (e == cudaSuccess && mixed) launch_tu_from_residual_dev(c->gs, c->D, c->f, c->x, c->r, c->Tu[next], N, s);
   c->x = x_own;
   return e;

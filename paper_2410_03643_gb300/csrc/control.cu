@@ -160,35 +160,57 @@ __global__ void __launch_bounds__(kCtlThreads) k_mgs_step(GmresState* gs, const 
 //   mode 2 (mixed refinement): outer += 1; relres = beta/fnorm; outer condition = beta/fnorm >= tol and
 //          outer < max_outer and it < max_it
 // In modes 1, 2 the new cycle starts from src = x (= r) with scale 1/beta.
+// When x's producer left block partials of ||x||^2 (mode 0: pa, na; mode 2: pa, na if the residual
+// came from the recurrence, else pb, nb), block 0 sums them in a fixed order and the other blocks
+// return; a count of 0 falls back to the sweep.
 __global__ void __launch_bounds__(kCtlThreads) k_norm_ctl(const double2* __restrict__ x, GmresState* gs, long long N,
                                                          double* partials, unsigned* counter, GridBarrier* bar,
                                                          SolveCfg cfg, int mode, cudaGraphConditionalHandle h_outer,
-                                                         int set_cond) {
+                                                         int set_cond, const double* __restrict__ pa, int na,
+                                                         const double* __restrict__ pb, int nb) {
   __shared__ double sh[32];
   __shared__ bool last;
   if (mode == 1 && gs->no_restart) {
     if (blockIdx.x == 0 && threadIdx.x == 0 && set_cond) cudaGraphSetConditional(h_outer, 0u);
     return;
   }
-  double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    const double2 v = x[i];
-    acc += v.x * v.x + v.y * v.y;
+  const double* pp = nullptr;
+  int pn = 0;
+  if (mode == 0) {
+    pp = pa;
+    pn = na;
+  } else if (mode == 2) {
+    const bool upd = gs->upd != 0;  // uniform
+    pp = upd ? pa : pb;
+    pn = upd ? na : nb;
   }
-  acc = block_sum_c(acc, sh);
-  if (threadIdx.x == 0) {
-    partials[blockIdx.x] = acc;
-    __threadfence();
-    last = (atomicAdd(counter, 1u) == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
   double s = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += ((volatile const double*)partials)[i];
-  s = block_sum_c(s, sh);
-  if (threadIdx.x != 0) return;
-  *counter = 0u;
+  if (pn > 0) {
+    if (blockIdx.x != 0) return;
+    for (int i = threadIdx.x; i < pn; i += blockDim.x) s += pp[i];
+    s = block_sum_c(s, sh);
+    if (threadIdx.x != 0) return;
+  } else {
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+      const double2 v = x[i];
+      acc = fma(v.x, v.x, acc);
+      acc = fma(v.y, v.y, acc);
+    }
+    acc = block_sum_c(acc, sh);
+    if (threadIdx.x == 0) {
+      partials[blockIdx.x] = acc;
+      __threadfence();
+      last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += ((volatile const double*)partials)[i];
+    s = block_sum_c(s, sh);
+    if (threadIdx.x != 0) return;
+    *counter = 0u;
+  }
   const double b = sqrt(s);
   gs->beta = b;
   gs->inv_beta = (b > 0.0) ? 1.0 / b : 0.0;
@@ -311,11 +333,15 @@ __global__ void k_resid_coeffs(GmresState* gs, int k_in, int upd_in, double err_
   gs->q[0] = t;
 }
 
-// r = sum_{i<k} q_i V_i + q_k inv_h w when gs->upd, k = gs->j if k_in < 0.
+// r = sum_{i<k} q_i V_i + q_k inv_h w when gs->upd, k = gs->j if k_in < 0; with nrm_part, each
+// block also leaves its share of ||r||^2 there for the norm kernel.
 __global__ void k_resid_update(const double2* __restrict__ V, long long ldv, const double2* __restrict__ w,
-                               const GmresState* gs, int k_in, double2* __restrict__ r, long long N) {
+                               const GmresState* gs, int k_in, double2* __restrict__ r, long long N,
+                               double* __restrict__ nrm_part) {
   if (!gs->upd) return;  // uniform
   __shared__ double q[kMaxM + 1];
+  __shared__ double sh[32];
+  double nacc = 0.0;
   const int k = k_in >= 0 ? k_in : gs->j;
   for (int t = threadIdx.x; t <= k; t += blockDim.x) q[t] = gs->q[t];
   __syncthreads();
@@ -329,6 +355,12 @@ __global__ void k_resid_update(const double2* __restrict__ V, long long ldv, con
       a.y += q[j] * v.y;
     }
     r[i] = a;
+    nacc = fma(a.x, a.x, nacc);
+    nacc = fma(a.y, a.y, nacc);
+  }
+  if (nrm_part) {
+    nacc = block_sum_c(nacc, sh);
+    if (threadIdx.x == 0) nrm_part[blockIdx.x] = nacc;
   }
 }
 
@@ -421,9 +453,12 @@ cudaError_t launch_mgs_step(GmresState* gs, const double2* V, long long ldv, dou
 
 void launch_norm_ctl(const double2* x, GmresState* gs, long long N, int blocks, double* partials, unsigned* counter,
                      GridBarrier* bar, const SolveCfg& cfg, int mode, cudaGraphConditionalHandle h_outer,
-                     int set_cond, cudaStream_t s) {
+                     int set_cond, cudaStream_t s, const double* pa, int na, const double* pb, int nb) {
   count_launch();
-  k_norm_ctl<<<blocks, kCtlThreads, 0, s>>>(x, gs, N, partials, counter, bar, cfg, mode, h_outer, set_cond);
+  // one block when every outcome has partials to sum
+  const bool partial_only = (mode == 0 && na > 0) || (mode == 2 && na > 0 && nb > 0);
+  k_norm_ctl<<<partial_only ? 1 : blocks, kCtlThreads, 0, s>>>(x, gs, N, partials, counter, bar, cfg, mode, h_outer,
+                                                               set_cond, pa, na, pb, nb);
 }
 void launch_cycle_begin(GmresState* gs, const SolveCfg& cfg, cudaGraphConditionalHandle h_inner,
                         cudaGraphConditionalHandle h_outer, int set_cond, cudaStream_t s) {
@@ -457,10 +492,11 @@ void launch_resid_coeffs(GmresState* gs, int k, int upd, double err, double tol,
   count_launch();
   k_resid_coeffs<<<1, 1, 0, s>>>(gs, k, upd, err, tol);
 }
+int resid_update_blocks(long long N) { return (int)ew_blocks_c(N); }
 void launch_resid_update(const double2* V, long long ldv, const double2* w, const GmresState* gs, int k,
-                         double2* r, long long N, cudaStream_t s) {
+                         double2* r, long long N, cudaStream_t s, double* nrm_part) {
   count_launch();
-  k_resid_update<<<ew_blocks_c(N), 256, 0, s>>>(V, ldv, w, gs, k, r, N);
+  k_resid_update<<<ew_blocks_c(N), 256, 0, s>>>(V, ldv, w, gs, k, r, N, nrm_part);
 }
 
 // Self-test of the bounded wait: one block arrives at a grid barrier whose arrival count is preset so

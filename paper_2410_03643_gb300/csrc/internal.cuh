@@ -14,6 +14,7 @@ constexpr int kMaxM = 256;  // largest supported restart length
 // Largest grid of a last matrix-product pass that hands its <v_0, w> partials to the Arnoldi kernel
 // (every block of that kernel sums them; larger grids keep the kernel's own first sweep).
 constexpr int kDot0MaxBlocks = 4096;
+constexpr int kNormPartMax = 4096;  // largest grid whose squared-norm partials a norm kernel sums
 
 // Number of kernels this library has launched in the process (all contexts).
 extern std::atomic<long long> g_kernel_launches;
@@ -77,9 +78,12 @@ cudaError_t launch_mgs_step(GmresState* gs, const double2* V, long long ldv, dou
                             double* partials, GridBarrier* bar, const SolveCfg& cfg,
                             cudaGraphConditionalHandle h_inner, int set_cond, int blocks, cudaStream_t s,
                             const double* pre_part = nullptr, int pre_n = 0);
+// pa/na, pb/nb: block partials of ||x||^2 left by x's producer (mode 0: pa; mode 2: pa when the
+// residual came from the recurrence, pb when from the product); a count 0 means sweep x
 void launch_norm_ctl(const double2* x, GmresState* gs, long long N, int blocks, double* partials, unsigned* counter,
                      GridBarrier* bar, const SolveCfg& cfg, int mode, cudaGraphConditionalHandle h_outer,
-                     int set_cond, cudaStream_t s);
+                     int set_cond, cudaStream_t s, const double* pa = nullptr, int na = 0,
+                     const double* pb = nullptr, int nb = 0);
 void launch_cycle_begin(GmresState* gs, const SolveCfg& cfg, cudaGraphConditionalHandle h_inner,
                         cudaGraphConditionalHandle h_outer, int set_cond, cudaStream_t s);
 void launch_backsolve_dev(GmresState* gs, cudaStream_t s);
@@ -92,7 +96,7 @@ constexpr double kUpdErr = 4e-7;  // relative error of an FP32 product, times be
 void launch_resid_coeffs(GmresState* gs, int k, int upd, double err, double tol, cudaStream_t s);
 // r = sum_{i<k} q_i V_i + q_k inv_h w when gs->upd (else nothing); k < 0: gs->j
 void launch_resid_update(const double2* V, long long ldv, const double2* w, const GmresState* gs, int k,
-                         double2* r, long long N, cudaStream_t s);
+                         double2* r, long long N, cudaStream_t s, double* nrm_part = nullptr);
 void launch_tu_from_residual_dev(const GmresState* gs, const double* D, const double2* f, const double2* x,
                                  const double2* r, double2* Tu, long long N, cudaStream_t s);
 void launch_gather_peeks(GmresState* const* gs, GmresPeek* out, int count, cudaStream_t s);
@@ -132,12 +136,16 @@ void launch_rhs_from_tu(const double2* u, const double2* Tu, const double* D, do
 void launch_prep_D(const double* D, float* D32, double2* dfac64, float2* dfac32, double omega, long long N,
                    cudaStream_t s);
 // mixed form, steady step: D, f = u_prev - i (Tu_prev - D u_prev) and the prep_D tables in one sweep
-void launch_step_prep(rfnse_ctx* c, const double2* uc, const double2* up, const double2* Tup, cudaStream_t s);
+void launch_step_prep(rfnse_ctx* c, const double2* uc, const double2* up, const double2* Tup, cudaStream_t s,
+                      double* nrm_part = nullptr);
+int step_prep_blocks(long long N);  // its grid (the number of partials it leaves)
+int resid_update_blocks(long long N);
 
 // ---- double-float Toeplitz passes (toep_df.cu) --------------------------------------------------
 bool toeplitz_df_available(const rfnse_ctx* c);
 cudaError_t run_toeplitz_df(rfnse_ctx* c, int axis, int half, bool first, const double2* z, const double* D,
-                            const double2* add, double2* w, double2 a, double2 b, const int* skip);
+                            const double2* add, double2* w, double2 a, double2 b, const int* skip,
+                            double* nrm_part = nullptr);
 void launch_setup_df(int log2L, const double* c64h0, const double* c64h1, void* tw, void* c0, void* c1,
                      cudaStream_t s);
 
@@ -224,6 +232,11 @@ struct rfnse_ctx {
   int coop_blocks = 1;
   double* dot_part = nullptr;        // kDot0MaxBlocks partials of <v_0, w> from the last product pass
   int dot0_blocks = 0;               // how many the last such launch wrote (0: none)
+  // block partials of squared norms left by the kernel that produced the vector, so that the solve's
+  // norm kernel only sums them: f (k_step_prep), r from the recurrence (k_resid_update), r from the
+  // double-float product (its last pass); kNormPartMax each
+  double* nrm_part = nullptr;        // 3 x kNormPartMax
+  int nrm_df_blocks = 0;             // partials the last double-float product wrote (0: none)
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;   // private stream that captures the loop bodies
   cudaStream_t cap_stream2 = nullptr;  // private stream that captures a stand-alone solve graph

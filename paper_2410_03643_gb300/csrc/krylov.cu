@@ -191,19 +191,28 @@ __global__ void k_rhs_from_tu(const double2* __restrict__ u, const double2* __re
 __global__ void k_step_prep(const double2* __restrict__ uc, const double2* __restrict__ up,
                             const double2* __restrict__ Tup, double* __restrict__ D, double2* __restrict__ f,
                             float* __restrict__ D32, double2* __restrict__ dfac64, float2* __restrict__ dfac32,
-                            double rho_dt, double omega, long long N) {
+                            double rho_dt, double omega, long long N, double* __restrict__ nrm_part) {
+  __shared__ double sh[32];
   const double w1 = omega + 1.0, two_w = 2.0 * omega;
+  double nacc = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     const double2 v = uc[i], uv = up[i], tv = Tup[i];
     const double d = rho_dt * (v.x * v.x + v.y * v.y);
     D[i] = d;
     const double px = tv.x - d * uv.x, py = tv.y - d * uv.y;
-    f[i] = make_double2(uv.x + py, uv.y - px);
+    const double2 fv = make_double2(uv.x + py, uv.y - px);
+    f[i] = fv;
+    nacc = fma(fv.x, fv.x, nacc);
+    nacc = fma(fv.y, fv.y, nacc);
     const double s = two_w / (w1 * w1 + d * d);
     const double2 fac = make_double2(s * w1, s * d);
     D32[i] = (float)d;
     dfac64[i] = fac;
     dfac32[i] = make_float2((float)fac.x, (float)fac.y);
+  }
+  if (nrm_part) {  // this block's share of ||f||^2 for the solve's norm kernel (uniform branch)
+    nacc = block_sum(nacc, sh);
+    if (threadIdx.x == 0) nrm_part[blockIdx.x] = nacc;
   }
 }
 
@@ -265,10 +274,12 @@ void launch_rhs_from_tu(const double2* u, const double2* Tu, const double* D, do
   count_launch();
   k_rhs_from_tu<<<ew_blocks(N), 256, 0, s>>>(u, Tu, D, f, N);
 }
-void launch_step_prep(rfnse_ctx* c, const double2* uc, const double2* up, const double2* Tup, cudaStream_t s) {
+int step_prep_blocks(long long N) { return (int)ew_blocks(N); }
+void launch_step_prep(rfnse_ctx* c, const double2* uc, const double2* up, const double2* Tup, cudaStream_t s,
+                      double* nrm_part) {
   count_launch();
   k_step_prep<<<ew_blocks(c->N), 256, 0, s>>>(uc, up, Tup, c->D, c->f, c->D32, c->dfac64, c->dfac32,
-                                              c->p.rho * c->p.dt, c->p.omega, c->N);
+                                              c->p.rho * c->p.dt, c->p.omega, c->N, nrm_part);
 }
 void launch_zero(double2* x, long long N, cudaStream_t s) { k_zero<<<ew_blocks(N), 256, 0, s>>>(x, N); }
 

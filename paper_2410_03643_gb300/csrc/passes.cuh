@@ -95,6 +95,8 @@ struct PassParams {
   // F_DOT0: v_0 (FP64, grid order) and the per-block partials (one per block of the launch)
   const double2* dot_v0;
   double* dot_part;
+  // double-float Toeplitz passes: when set, each block's share of ||result||^2
+  double* nrm_part;
 };
 
 // Sum of v over the block, written by thread 0 to *out; every thread of the block must call it.  The

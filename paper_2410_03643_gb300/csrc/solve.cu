@@ -46,14 +46,20 @@ cudaError_t prepare_D(rfnse_ctx* c, const double* D) {
 // w = add + a z + b (T - D) z in FP64 (the Toeplitz products by circulant embedding).  In the mixed
 // form the FFTs of the embedding run in double-float (toep_df.cu) when every axis has a fixed FFT.
 cudaError_t run_matvec_fp64(rfnse_ctx* c, const double2* z, const double* D, double2* w, const double2* add,
-                            double2 a, double2 b, int half, const int* skip) {
+                            double2 a, double2 b, int half, const int* skip, double* nrm_part) {
   cudaStream_t s = c->stream;
   cudaError_t e;
   const int h = half ? 1 : 0;
+  c->nrm_df_blocks = 0;
   if (c->p.precision == 1 && toeplitz_df_available(c)) {
-    if ((e = run_toeplitz_df(c, 0, h, true, z, D, add, w, a, b, skip)) != cudaSuccess) return e;
+    // the last pass may leave the partials of ||w||^2 (c->nrm_df_blocks of them)
+    if ((e = run_toeplitz_df(c, 0, h, true, z, D, add, w, a, b, skip, c->d == 1 ? nrm_part : nullptr)) !=
+        cudaSuccess)
+      return e;
     for (int a2 = 1; a2 < c->d; ++a2)
-      if ((e = run_toeplitz_df(c, a2, h, false, z, nullptr, w, w, a, b, skip)) != cudaSuccess) return e;
+      if ((e = run_toeplitz_df(c, a2, h, false, z, nullptr, w, w, a, b, skip,
+                               a2 == c->d - 1 ? nrm_part : nullptr)) != cudaSuccess)
+        return e;
     return cudaSuccess;
   }
   {
@@ -365,7 +371,8 @@ static cudaError_t arnoldi_step_dev(rfnse_ctx* c, int half, const SolveCfg& cfg,
 // Record the solve of R x = f (c->f, c->x, c->D fixed) for one precision and half flag at the current
 // capture position of stream s, which is capturing into graph g: x = 0, ||f||, then the outer WHILE
 // node.  The loop bodies are captured on the context's private body stream.
-cudaError_t capture_solve(rfnse_ctx* c, int mixed, int half, cudaGraph_t g, cudaStream_t s) {
+cudaError_t capture_solve(rfnse_ctx* c, int mixed, int half, cudaGraph_t g, cudaStream_t s, const double* f_part,
+                          int f_n) {
   const long long N = c->N;
   const SolveCfg cfg = make_cfg(c, mixed);
   cudaStream_t user = c->stream;
@@ -386,7 +393,7 @@ cudaError_t capture_solve(rfnse_ctx* c, int mixed, int half, cudaGraph_t g, cuda
   // solve start: x = 0, beta = ||f||, outer condition
   c->stream = s;
   launch_zero(c->x, N, s);
-  launch_norm_ctl(c->f, c->gs, N, c->red_blocks, c->partials, c->counter, c->bar, cfg, 0, ho, 1, s);
+  launch_norm_ctl(c->f, c->gs, N, c->red_blocks, c->partials, c->counter, c->bar, cfg, 0, ho, 1, s, f_part, f_n);
   if ((e = add_while_node(s, ho, &obody)) != cudaSuccess) return fail(e);
   // outer body: cycle start, inner loop, solution update, residual and the outer condition
   c->stream = bs;
@@ -401,10 +408,15 @@ cudaError_t capture_solve(rfnse_ctx* c, int mixed, int half, cudaGraph_t g, cuda
   if (mixed) {
     launch_combine_f32_add_dev(c->Z32, N, c->gs, c->x, N, bs);
     launch_resid_coeffs(c->gs, -1, -1, 0.0, cfg.tol, bs);
-    if ((e = run_matvec_fp64(c, c->x, c->D, c->r, c->f, kMinusOne, kMinusI, half, &c->gs->upd)) != cudaSuccess)
+    // the residual (product or recurrence, whichever runs) leaves the partials of ||r||^2
+    double* part_df = c->nrm_part + kNormPartMax;
+    double* part_upd = c->nrm_part + 2 * kNormPartMax;
+    if ((e = run_matvec_fp64(c, c->x, c->D, c->r, c->f, kMinusOne, kMinusI, half, &c->gs->upd, part_df)) !=
+        cudaSuccess)
       return fail(e);
-    launch_resid_update(c->V, N, c->w, c->gs, -1, c->r, N, bs);
-    launch_norm_ctl(c->r, c->gs, N, c->red_blocks, c->partials, c->counter, c->bar, cfg, 2, ho, 1, bs);
+    launch_resid_update(c->V, N, c->w, c->gs, -1, c->r, N, bs, part_upd);
+    launch_norm_ctl(c->r, c->gs, N, c->red_blocks, c->partials, c->counter, c->bar, cfg, 2, ho, 1, bs, part_upd,
+                    resid_update_blocks(N), part_df, c->nrm_df_blocks);
   } else {
     launch_combine_dev(c->V, N, c->gs, c->r, N, bs);
     if ((e = run_precon<double, double2, double2, double2, double2, false, false>(

@@ -4,8 +4,10 @@
 
 namespace rfnse {
 
+// nrm_part: when the double-float passes run, the last leaves block partials of ||w||^2 there
+// (c->nrm_df_blocks of them; 0 when not)
 cudaError_t run_matvec_fp64(rfnse_ctx* c, const double2* z, const double* D, double2* w, const double2* add,
-                            double2 a, double2 b, int half, const int* skip);
+                            double2 a, double2 b, int half, const int* skip, double* nrm_part = nullptr);
 cudaError_t run_dst(rfnse_ctx* c, int axis, const double2* in, double2* out, int precision);
 cudaError_t run_toeplitz(rfnse_ctx* c, int axis, const double2* in, double2* out, int half);
 cudaError_t run_apply_prec(rfnse_ctx* c, const double2* v, double2* z, const double* D, int half, int precision);
@@ -16,6 +18,8 @@ rfnse_status time_step(rfnse_ctx* c, int* iters, double* relres);
 rfnse_status tban_solve(rfnse_ctx* c, const double* D, const double2* f, double2* x, int half, int* iters,
                         double* relres);
 cudaError_t prepare_D(rfnse_ctx* c, const double* D);
-cudaError_t capture_solve(rfnse_ctx* c, int mixed, int half, cudaGraph_t g, cudaStream_t s);
+// f_part / f_n: block partials of ||f||^2 left by f's producer in the same graph (f_n = 0: none)
+cudaError_t capture_solve(rfnse_ctx* c, int mixed, int half, cudaGraph_t g, cudaStream_t s,
+                          const double* f_part = nullptr, int f_n = 0);
 
 }  // namespace rfnse

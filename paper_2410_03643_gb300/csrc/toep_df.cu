@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_toeplitz_df(const PassParam
   const double2* accin = reinterpret_cast<const double2*>(p.acc_in);
   double2* accout = reinterpret_cast<double2*>(p.acc_out);
   const double* D = reinterpret_cast<const double*>(p.Dr);
+  double nacc = 0.0;
   for (int e = tid; e < B * n; e += nthr) {
     int l, pos;
     map(e, l, pos);
@@ -123,8 +124,12 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_toeplitz_df(const PassParam
       t.y -= Dj * z.y;
       acc = cadd(acc, coef_mul(p.ca_code, p.ca, z));
     }
-    accout[g] = cadd(acc, coef_mul(p.cb_code, p.cb, t));
+    const double2 out = cadd(acc, coef_mul(p.cb_code, p.cb, t));
+    accout[g] = out;
+    nacc = fma(out.x, out.x, nacc);
+    nacc = fma(out.y, out.y, nacc);
   }
+  if (p.nrm_part) block_sum_store(nacc, p.nrm_part + blockIdx.x);  // share of ||result||^2 (uniform)
 }
 
 template <int LOG2L>
@@ -154,7 +159,8 @@ bool toeplitz_df_available(const rfnse_ctx* c) {
 
 // One Toeplitz pass along `axis` in double-float: first = the x-pass with diagonal and coupling.
 cudaError_t run_toeplitz_df(rfnse_ctx* c, int axis, int half, bool first, const double2* z, const double* D,
-                            const double2* add, double2* w, double2 a, double2 b, const int* skip) {
+                            const double2* add, double2* w, double2 a, double2 b, const int* skip,
+                            double* nrm_part) {
   PassParams p{};
   p.n = c->n[axis];
   p.L = c->L[axis];
@@ -186,6 +192,10 @@ cudaError_t run_toeplitz_df(rfnse_ctx* c, int axis, int half, bool first, const 
   }
   if (grid <= 0) return cudaSuccess;
   if (p.B * p.nt > kPassMaxThreads || p.B * p.nt < 1) return cudaErrorInvalidConfiguration;
+  if (nrm_part) {  // partials of ||w||^2 for the norm kernel, if it can sum this many
+    p.nrm_part = grid <= kNormPartMax ? nrm_part : nullptr;
+    c->nrm_df_blocks = grid <= kNormPartMax ? (int)grid : 0;
+  }
   const size_t smem = (size_t)p.B * fft_line_stride(p.L) * sizeof(cdf);
   // kernel-class profiling (rfnse_profile): kind = Toeplitz flag | RFNSE_K_DF
   const int kind = (first ? F_TOEP_X : F_TOEP_ACC) | RFNSE_K_DF;
