@@ -28,19 +28,36 @@ __global__ void k_coefficients(double* c, int nmax, double alpha) {
 //     'taudiagonal'), i.e. c_0 + 2 sum_m c_m cos(pi m k/(n+1)).
 //   tw: the per-stage twiddle table of a length-L FFT, FP64 in the layout of fft_line.cuh, FP32 in
 //     that of fft_fixed.cuh for the lengths the FP32 passes compile with a fixed FFT.
+// k_axis_eigen computes circ and lam, k_axis_tables the twiddles.
+// The eigenvalue sums, one block of kEigThreads per k: thread t takes m = n - 1 - t, n - 1 - t - T, ...
+// (each thread's terms in decreasing m), then a fixed-order block reduction (warp shuffles, then the
+// warps in order), so every table entry is reproducible.
+constexpr int kEigThreads = 128;
+__global__ void __launch_bounds__(kEigThreads) k_axis_eigen(const double* __restrict__ c, int n, int L,
+                                                           double* __restrict__ lam, double* __restrict__ circ) {
+  __shared__ double red[kEigThreads / 32];
+  const int k = blockIdx.x;
+  const int period = L;  // cos(2 pi m k / L) has period L in (m k)
+  double s = 0.0;
+  for (int m = n - 1 - (int)threadIdx.x; m >= 1; m -= kEigThreads) {
+    const long long mk = ((long long)m * k) % period;
+    s += c[m] * cospi(2.0 * (double)mk / (double)L);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double t = 0.0;
+  for (int w = 0; w < kEigThreads / 32; ++w) t += red[w];
+  const double v = c[0] + 2.0 * t;
+  circ[k] = v;
+  if (k >= 1 && k <= n) lam[k - 1] = v;
+}
+
 __global__ void k_axis_tables(const double* __restrict__ c, int n, int L, double* __restrict__ lam,
                               double* __restrict__ circ, double2* __restrict__ tw64, float2* __restrict__ tw32) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= L) return;
-  const int period = L;  // cos(2 pi m k / L) has period L in (m k)
-  double s = 0.0;
-  for (int m = n - 1; m >= 1; --m) {
-    const long long mk = ((long long)m * k) % period;
-    s += c[m] * cospi(2.0 * (double)mk / (double)L);
-  }
-  const double v = c[0] + 2.0 * s;
-  circ[k] = v;
-  if (k >= 1 && k <= n) lam[k - 1] = v;
   // twiddle entry k of the per-stage table of fft_line.cuh: stage Ns holds W_{4Ns}^{r kk},
   // r = 1..3, kk = 0..Ns-1, at (r-1) Ns + kk of its segment
   int log2L = 0;
@@ -180,7 +197,8 @@ void launch_setup_coefficients(double* c, int nmax, double alpha, cudaStream_t s
 
 void launch_setup_axis(const double* c, int n, int L, double* lam, double* circ, double2* tw64, float2* tw32,
                        cudaStream_t s) {
-  count_launch();
+  count_launch(2);
+  k_axis_eigen<<<L, kEigThreads, 0, s>>>(c, n, L, lam, circ);
   k_axis_tables<<<(L + 127) / 128, 128, 0, s>>>(c, n, L, lam, circ, tw64, tw32);
 }
 
