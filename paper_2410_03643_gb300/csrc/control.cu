@@ -25,7 +25,7 @@ __device__ __forceinline__ double block_sum_c(double v, double* sh) {
 
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).  The wait is bounded: after
 // kMaxSpin polls the block records the failure in *err and continues.
-__device__ __forceinline__ void grid_barrier(GridBarrier* b, int* err) {
+__device__ __forceinline__ void grid_barrier_global(GridBarrier* b, int* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* vgen = &b->gen;
@@ -49,6 +49,15 @@ __device__ __forceinline__ void grid_barrier(GridBarrier* b, int* err) {
     __threadfence();
   }
   __syncthreads();
+}
+
+// A one-block grid needs only the block barrier (uniform branch); larger grids use the global protocol.
+__device__ __forceinline__ void grid_barrier(GridBarrier* b, int* err) {
+  if (gridDim.x == 1) {
+    __syncthreads();
+    return;
+  }
+  grid_barrier_global(b, err);
 }
 
 // The same value in every block: the partials summed in a fixed order.
@@ -425,6 +434,7 @@ int coop_blocks_for(long long N) {
   // Small grids (up to a few 10^5 points) are bound by the barriers between the MGS passes: one block
   // per SM is faster and leaves room for other instances' kernels; large grids stream their vectors
   // and take two blocks per SM (measured on the 2-D 511^2, batched and 3-D 255^3 workloads).
+  if (N <= 4096) return 1;  // a few points per thread: block barriers only, no grid-wide protocol
   const int use = (N >= (1LL << 22)) ? 2 : 1;
   long long b = (long long)sms * (per_sm < use ? per_sm : use);
   const long long need = (N + kCtlThreads - 1) / kCtlThreads;
@@ -502,7 +512,7 @@ void launch_resid_update(const double2* V, long long ldv, const double2* w, cons
 // Self-test of the bounded wait: one block arrives at a grid barrier whose arrival count is preset so
 // that the barrier can never complete (a release that nothing performs); grid_barrier must give up
 // after kMaxSpin polls, record the failure and return.
-__global__ void k_selftest_wait(GridBarrier* b, int* err) { grid_barrier(b, err); }
+__global__ void k_selftest_wait(GridBarrier* b, int* err) { grid_barrier_global(b, err); }
 
 }  // namespace rfnse
 
