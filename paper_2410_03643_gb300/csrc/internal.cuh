@@ -130,8 +130,6 @@ void launch_start_cycle(GmresState* gs, double ref, double tol, cudaStream_t s);
 void launch_tu_from_residual(const double* D, const double2* f, const double2* x, const double2* r, double2* Tu,
                              double scale, long long N, cudaStream_t s);
 // f = u - i (Tu - D u)
-void launch_rhs_from_tu(const double2* u, const double2* Tu, const double* D, double2* f, long long N,
-                        cudaStream_t s);
 // D32 = D, dfac = 2w((w+1) + iD)/((w+1)^2 + D^2) in FP64 and FP32
 void launch_prep_D(const double* D, float* D32, double2* dfac64, float2* dfac32, double omega, long long N,
                    cudaStream_t s);

@@ -174,20 +174,9 @@ __global__ void k_tu_from_residual(const double* __restrict__ D, const double2* 
   }
 }
 
-// Right-hand side f = u - i (T u - D u) from a cached T u.
-__global__ void k_rhs_from_tu(const double2* __restrict__ u, const double2* __restrict__ Tu,
-                              const double* __restrict__ D, double2* __restrict__ f, long long N) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    const double2 uv = u[i], tv = Tu[i];
-    const double d = D[i];
-    const double px = tv.x - d * uv.x, py = tv.y - d * uv.y;
-    f[i] = make_double2(uv.x + py, uv.y - px);
-  }
-}
-
-// One steady step's pointwise set-up in the mixed form, with T u^{n-1} cached: D = rho dt |u^n|^2,
-// f = u^{n-1} - i (T u^{n-1} - D u^{n-1}) and the tables of k_prep_D, in one sweep (the same
-// arithmetic as k_diag, k_rhs_from_tu and k_prep_D in turn).
+// One steady step's pointwise set-up in the mixed form, with T u^{n-1} cached: D = rho dt |u^n|^2
+// (as k_diag), the right-hand side f = u^{n-1} - i (T u^{n-1} - D u^{n-1}) (paper Sec. 2, the block
+// form's f = -i b with b = (T - D + iI) u^{n-1}) and the tables of k_prep_D, in one sweep.
 __global__ void k_step_prep(const double2* __restrict__ uc, const double2* __restrict__ up,
                             const double2* __restrict__ Tup, double* __restrict__ D, double2* __restrict__ f,
                             float* __restrict__ D32, double2* __restrict__ dfac64, float2* __restrict__ dfac32,
@@ -268,11 +257,6 @@ void launch_tu_from_residual(const double* D, const double2* f, const double2* x
                              double scale, long long N, cudaStream_t s) {
   count_launch();
   k_tu_from_residual<<<ew_blocks(N), 256, 0, s>>>(D, f, x, r, Tu, scale, N);
-}
-void launch_rhs_from_tu(const double2* u, const double2* Tu, const double* D, double2* f, long long N,
-                        cudaStream_t s) {
-  count_launch();
-  k_rhs_from_tu<<<ew_blocks(N), 256, 0, s>>>(u, Tu, D, f, N);
 }
 int step_prep_blocks(long long N) { return (int)ew_blocks(N); }
 void launch_step_prep(rfnse_ctx* c, const double2* uc, const double2* up, const double2* Tup, cudaStream_t s,
