@@ -9,7 +9,14 @@ form (FP32 transforms inside FGMRES, FP64 Arnoldi/Givens, the refinement residua
 beside it, with the difference between the two trajectories.  DOF = complex grid unknowns.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload 2d|3d|1d|batched|adjoint|comparators|omega]
+                  [--workload 2d|3d|1d|batched|adjoint|comparators|omega] [--instances K]
+  python bench.py --alu-probe | --arnoldi-probe
+
+The JSON line's roofline objects are the three largest kernel classes of the step, each timed launch
+by launch (CUDA events) in a further serial run with host-driven loops: the cooperative Arnoldi
+kernel, the FP32 fused x-pass and the double-float residual x-pass.  --instances K runs K 511^2
+instances instead of three (the throughput saturates from about 6 on); --arnoldi-probe times the
+Arnoldi kernel alone per column j; --alu-probe measures the FP64 and FP32 FMA rates.
 
 Other workloads: 3d (255^3, mixed), 1d (n = 1023), batched (64 independent 2-D instances with grids
 drawn from {127, 255, 511}^2: one step = one graph launch advancing all of them), adjoint (255^2,
