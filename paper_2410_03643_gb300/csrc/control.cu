@@ -117,6 +117,22 @@ __global__ void __launch_bounds__(kCtlThreads) k_mgs_step(GmresState* gs, const 
       acc = fma(a.y, wv.y, acc);
     }
     acc = block_sum_c(acc, sh);
+    if (i == j + 1 && nb > 1) {
+      // the norm: only one thread needs it, so the last block to arrive sums the partials and
+      // finishes the step while the others leave (no wait)
+      __shared__ bool last_blk;
+      if (threadIdx.x == 0) {
+        buf[blockIdx.x] = acc;
+        __threadfence();
+        last_blk = (atomicAdd(&bar->done, 1u) == (unsigned)nb - 1u);
+      }
+      __syncthreads();
+      if (!last_blk) return;
+      __threadfence();
+      nrm2 = fixed_sum(buf, nb, sh);
+      if (threadIdx.x == 0) bar->done = 0u;
+      break;
+    }
     if (threadIdx.x == 0) buf[blockIdx.x] = acc;
     __threadfence();
     grid_barrier(bar, &gs->err);
@@ -128,7 +144,7 @@ __global__ void __launch_bounds__(kCtlThreads) k_mgs_step(GmresState* gs, const 
       nrm2 = s;
     }
   }
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  if (threadIdx.x != 0) return;  // one block is left: the last to arrive (or the only one)
   double* Hc = gs->H + (size_t)j * (kMaxM + 1);
   const double hnext = sqrt(nrm2);
   Hc[j + 1] = hnext;
@@ -240,6 +256,7 @@ __global__ void __launch_bounds__(kCtlThreads) k_norm_ctl(const double2* __restr
     gs->done = isfinite(b) ? 0 : 3;
     gs->relres = (b > 0.0) ? 1.0 : 0.0;
     bar->count = 0u;
+    bar->done = 0u;
     cont = (b > 0.0 && isfinite(b)) ? 1u : 0u;
   } else {
     gs->outer += 1;

@@ -69,6 +69,7 @@ struct SolveCfg {
 struct GridBarrier {
   unsigned count;
   unsigned gen;
+  unsigned done;  // arrivals at the Arnoldi kernel's last reduction (reset by the last block)
 };
 
 // ---- device-side control (control.cu) -----------------------------------------------------------
