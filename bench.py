@@ -70,7 +70,7 @@ def measured_hbm_gbs():
 TRAFFIC_FP32_FUSED_X = {"2d": 5288960 + 0}
 # DRAM read+write per launch of the cooperative Arnoldi kernel (ncu, 2-D 511^2: mean of 10 consecutive
 # launches, columns j = 1,0,1,2,0,1,0,1,2,0, the mix of the bench's solves; (j + 2) x 4.2 MB each)
-TRAFFIC_ARNOLDI = {"2d": 11740262 + 0}
+TRAFFIC_ARNOLDI = {"2d": 11744538 + 0}
 # DRAM read+write per launch of the double-float residual x-pass (ncu, 2-D 511^2, steady launch: the
 # launches alternate 6.36 / 10.54 MB, the larger after the first step's extra product)
 TRAFFIC_DF_TOEP_X = {"2d": 6360320 + 0}
