@@ -140,8 +140,10 @@ rfnse_ctx* rfnse_batch_context(rfnse_batch* b, int i);
    all are past it, one time step of the whole batch is a single CUDA graph launch: per instance its
    right-hand side, its solve with device-decided loops, the update of the mixed form's cached T u
    and the rotation of its history, then a gather of every instance's statistics.  iters, relres
-   (host, may be NULL): nsteps * count values, step-major ([s * count + i]).  Errors: EINVAL, ECUDA,
-   ENOCONV (every step is still taken), ENUMERIC, ETIMEOUT. */
+   (host, may be NULL): nsteps * count values, step-major ([s * count + i]).  An instance that fails
+   does not stop the others: every instance takes (or fails) the step, then the call returns the first
+   failure, rfnse_batch_last_error naming its instance, without taking further steps.  Errors: EINVAL,
+   ECUDA, ENOCONV (every step is still taken), ENUMERIC, ETIMEOUT. */
 int rfnse_batch_run(rfnse_batch* b, int nsteps, int* iters, double* relres);
 
 /* ---- reverse pass: gradients of a loss of u^N ---------------------------------------------------
@@ -231,11 +233,14 @@ int rfnse_get_coefficients(rfnse_ctx* ctx, double* c, double* lam);
    Scratch: the coefficient, eigenvalue, twiddle and factor tables and the intermediate grid vectors live
    in one static device array of about 17 MB that every GPU loading this library holds until the
    process exits.  Limit: N = n[0]*n[1]*n[2] <= 262144 (e.g. 511 x 511), each n[a] + 1 a power of two
-   in [4, 2048]; larger grids return RFNSE_EINVAL (use rfnse_create).  The first call on a device
-   looks up the array's device address (cudaGetSymbolAddress) for that device; make that first call
-   before any stream capture.  All calls on a device share the array and each overwrites what it
-   reads, so nothing needs clearing between calls, but calls whose work overlaps on the GPU race on
-   it: serialise them.  Errors: EINVAL, ECUDA. */
+   in [4, 2048]; larger grids return RFNSE_EINVAL (use rfnse_create).  p is checked as rfnse_create
+   checks it (d, grid, box, alpha, rho, dt, omega): what rfnse_create refuses is refused here.  Every
+   call looks up the array's address on the current device (cudaGetSymbolAddress) and waits for the
+   stream to finish (cudaStreamSynchronize) before returning.  All calls on a device share the array
+   and each overwrites what it reads, so nothing needs clearing between calls, but calls whose work
+   overlaps on the GPU race on it: serialise them.  A CUDA error already pending in the calling thread
+   (from earlier work of the caller) is left in place for the caller to read, and the call then returns
+   RFNSE_ECUDA without doing any work.  Errors: EINVAL, ECUDA. */
 int rfnse_apply_prec_static(const rfnse_params* p, const void* v, void* z, const double* D, int half,
                             void* stream);
 
@@ -251,6 +256,14 @@ int rfnse_selftest_bounded_wait(void* stream, int* err, double* ms);
 
 /* Number of CUDA kernels this library has launched in the calling process (all contexts). */
 long long rfnse_launch_count(void);
+
+/* Test hook for the allocation-failure paths (the paper has no counterpart): after `after` more
+   successful device or pinned-host allocations by contexts, batches and reverse-pass tapes of this
+   process, every later one fails as if the GPU were out of memory, so the call that needed it returns
+   RFNSE_ENOMEM (rfnse_create and rfnse_batch_create with *out = NULL and nothing leaked;
+   rfnse_tape_forward with the context still usable).  after < 0 removes the limit (the default).  The
+   limit is process-wide; no GPU memory is used up to provoke the failure.  Always RFNSE_OK. */
+int rfnse_test_fail_allocations(long long after);
 
 /* Measure the FMA throughput of the current device (flop/s, 2 flops per FMA) in FP64 (fp64 = 1) or
    FP32 (fp64 = 0) with independent FMA chains on 8 blocks of 256 threads per SM, timed with CUDA

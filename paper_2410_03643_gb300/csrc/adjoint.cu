@@ -169,7 +169,7 @@ int rfnse_tape_forward(rfnse_ctx* c, const void* u0, int nsteps, int every, void
     cudaFree(c->tape);
     c->tape = nullptr;
     c->tape_vecs = 0;
-    const cudaError_t e = cudaMalloc((void**)&c->tape, bytes * t.total());
+    const cudaError_t e = dev_alloc((void**)&c->tape, bytes * t.total());
     if (e != cudaSuccess) {
       cudaGetLastError();
       c->tape = nullptr;
@@ -179,7 +179,7 @@ int rfnse_tape_forward(rfnse_ctx* c, const void* u0, int nsteps, int every, void
     c->tape_vecs = t.total();
   }
   if (!c->adj_red) {
-    const cudaError_t e = cudaMalloc((void**)&c->adj_red, sizeof(double) * (kAdjMaxBlocks + 1));
+    const cudaError_t e = dev_alloc((void**)&c->adj_red, sizeof(double) * (kAdjMaxBlocks + 1));
     if (e != cudaSuccess) {
       cudaGetLastError();
       c->adj_red = nullptr;
@@ -336,7 +336,7 @@ int rfnse_adjoint_solve(rfnse_ctx* c, const double* D, const void* g, void* lam,
                         double* relres) {
   if (!c || !D || !g || !lam || g == lam) return RFNSE_EINVAL;
   if (!c->adj_red) {
-    const cudaError_t e = cudaMalloc((void**)&c->adj_red, sizeof(double) * (kAdjMaxBlocks + 1));
+    const cudaError_t e = dev_alloc((void**)&c->adj_red, sizeof(double) * (kAdjMaxBlocks + 1));
     if (e != cudaSuccess) {
       cudaGetLastError();
       c->adj_red = nullptr;

@@ -1,4 +1,5 @@
 // C ABI (include/rfnse.h): context life cycle, state, time stepping and building blocks.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -10,8 +11,59 @@
 using namespace rfnse;
 
 namespace {
-
 bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+}  // namespace
+
+namespace rfnse {
+
+const char* validate_problem(const rfnse_params* p) {
+  if (!p) return "params is NULL";
+  if (p->d < 1 || p->d > 3) return "d must be 1, 2 or 3";
+  for (int a = 0; a < p->d; ++a) {
+    if (p->n[a] < 3 || p->n[a] > 2047 || !is_pow2((long long)p->n[a] + 1))
+      return "n[a] + 1 must be a power of two between 4 and 2048";
+    if (!(p->hi[a] > p->lo[a]) || !std::isfinite(p->hi[a] - p->lo[a])) return "need hi[a] > lo[a]";
+  }
+  if (!(p->alpha > 1.0 && p->alpha <= 2.0)) return "alpha must satisfy 1 < alpha <= 2";
+  if (!(p->rho >= 0.0) || !std::isfinite(p->rho)) return "rho must be finite and >= 0";
+  if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return "dt must be finite and > 0";
+  if (!(p->omega > 0.0) || !std::isfinite(p->omega)) return "omega must be finite and > 0";
+  return nullptr;
+}
+
+}  // namespace rfnse
+
+namespace {
+// Allocations still allowed before every later one fails (-1: no limit); rfnse_test_fail_allocations.
+std::atomic<long long> g_alloc_budget{-1};
+
+bool take_alloc_budget() {
+  long long b = g_alloc_budget.load();
+  while (b >= 0) {
+    if (b == 0) return false;
+    if (g_alloc_budget.compare_exchange_weak(b, b - 1)) return true;
+  }
+  return true;
+}
+}  // namespace
+
+namespace rfnse {
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (!take_alloc_budget()) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t host_alloc_pinned(void** p, size_t bytes) {
+  *p = nullptr;
+  if (!take_alloc_budget()) return cudaErrorMemoryAllocation;
+  return cudaMallocHost(p, bytes);
+}
+
+}  // namespace rfnse
+
+namespace {
 
 int ilog2(long long v) {
   int r = 0;
@@ -23,7 +75,7 @@ template <typename T>
 cudaError_t dalloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) return cudaSuccess;
-  return cudaMalloc((void**)p, count * sizeof(T));
+  return dev_alloc((void**)p, count * sizeof(T));
 }
 
 void free_ctx(rfnse_ctx* c) {
@@ -98,17 +150,7 @@ void free_ctx(rfnse_ctx* c) {
 }
 
 const char* validate(const rfnse_params* p) {
-  if (!p) return "params is NULL";
-  if (p->d < 1 || p->d > 3) return "d must be 1, 2 or 3";
-  for (int a = 0; a < p->d; ++a) {
-    if (p->n[a] < 3 || p->n[a] > 2047 || !is_pow2((long long)p->n[a] + 1))
-      return "n[a] + 1 must be a power of two between 4 and 2048";
-    if (!(p->hi[a] > p->lo[a]) || !std::isfinite(p->hi[a] - p->lo[a])) return "need hi[a] > lo[a]";
-  }
-  if (!(p->alpha > 1.0 && p->alpha <= 2.0)) return "alpha must satisfy 1 < alpha <= 2";
-  if (!(p->rho >= 0.0) || !std::isfinite(p->rho)) return "rho must be finite and >= 0";
-  if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return "dt must be finite and > 0";
-  if (!(p->omega > 0.0) || !std::isfinite(p->omega)) return "omega must be finite and > 0";
+  if (const char* why = validate_problem(p)) return why;
   if (p->restart < 1 || p->restart > kMaxM) return "restart must be in 1..256";
   if (p->max_it < 1) return "max_it must be >= 1";
   if (!(p->tol > 0.0)) return "tol must be > 0";
@@ -237,8 +279,8 @@ int rfnse_create(const rfnse_params* p, void* stream, rfnse_ctx** out) {
     for (int a = 0; a < c->d; ++a) all = all && fixed_fft_length(c->log2L[a]);
     if (all) {
       for (int a = 0; a < c->d; ++a) {
-        chk(cudaMalloc(&c->twdf[a], 16 * (size_t)c->L[a]));
-        for (int h = 0; h < 2; ++h) chk(cudaMalloc(&c->circdf[h][a], 8 * (size_t)c->L[a]));
+        chk(dev_alloc(&c->twdf[a], 16 * (size_t)c->L[a]));
+        for (int h = 0; h < 2; ++h) chk(dev_alloc(&c->circdf[h][a], 8 * (size_t)c->L[a]));
       }
     }
   }
@@ -254,7 +296,7 @@ int rfnse_create(const rfnse_params* p, void* stream, rfnse_ctx** out) {
   chk(dalloc(&c->partials, 1024));
   chk(dalloc(&c->counter, 1));
   chk(dalloc(&c->gs, 1));
-  if (e == cudaSuccess) chk(cudaMallocHost((void**)&c->peek, sizeof(GmresPeek)));
+  if (e == cudaSuccess) chk(host_alloc_pinned((void**)&c->peek, sizeof(GmresPeek)));
   if (e != cudaSuccess) {
     g_create_error = std::string("allocation failed: ") + cudaGetErrorString(e);
     cudaGetLastError();
@@ -436,6 +478,11 @@ int rfnse_get_coefficients(rfnse_ctx* c, double* cc, double* lam) {
 }
 
 long long rfnse_launch_count(void) { return g_kernel_launches.load(); }
+
+int rfnse_test_fail_allocations(long long after) {
+  g_alloc_budget.store(after < 0 ? -1 : after);
+  return RFNSE_OK;
+}
 
 int rfnse_profile(rfnse_ctx* c, int kind) {
   if (!c || kind < 0) return RFNSE_EINVAL;

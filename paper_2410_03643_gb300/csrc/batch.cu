@@ -195,9 +195,9 @@ int rfnse_batch_create(const rfnse_params* params, int count, void* stream, rfns
     for (auto& e : b->events)
       if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) st = RFNSE_ECUDA;
     if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) st = RFNSE_ECUDA;
-    if (cudaMalloc((void**)&b->d_gs, sizeof(GmresState*) * count) != cudaSuccess ||
-        cudaMalloc((void**)&b->d_peeks, sizeof(GmresPeek) * count) != cudaSuccess ||
-        cudaMallocHost((void**)&b->h_peeks, sizeof(GmresPeek) * count) != cudaSuccess)
+    if (dev_alloc((void**)&b->d_gs, sizeof(GmresState*) * count) != cudaSuccess ||
+        dev_alloc((void**)&b->d_peeks, sizeof(GmresPeek) * count) != cudaSuccess ||
+        host_alloc_pinned((void**)&b->h_peeks, sizeof(GmresPeek) * count) != cudaSuccess)
       st = RFNSE_ENOMEM;
   }
   if (st == RFNSE_OK) {
@@ -234,19 +234,23 @@ int rfnse_batch_run(rfnse_batch* b, int nsteps, int* iters, double* relres) {
   for (int s = 0; s < nsteps; ++s) {
     bool all_steady = true;
     for (rfnse_ctx* c : b->ctx) all_steady = all_steady && steady(c);
+    // a failing instance does not stop the others' step: every instance takes this step (or fails it),
+    // then the first failure is reported
+    int fail = RFNSE_OK;
     if (!all_steady) {  // first steps: every instance on its own (host-driven) until all are steady
       for (int i = 0; i < b->count; ++i) {
         int it = 0;
         double rr = 0.0;
         const int st = rfnse_run(b->ctx[i], 1, nullptr, &it, &rr, 1);
-        if (st != RFNSE_OK && st != RFNSE_ENOCONV) {
+        if (st != RFNSE_OK && st != RFNSE_ENOCONV && fail == RFNSE_OK) {
           b->err = "instance " + std::to_string(i) + ": " + rfnse_last_error(b->ctx[i]);
-          return st;
+          fail = st;
         }
         if (st == RFNSE_ENOCONV) worst = RFNSE_ENOCONV;
         if (iters) iters[(size_t)s * b->count + i] = it;
         if (relres) relres[(size_t)s * b->count + i] = rr;
       }
+      if (fail != RFNSE_OK) return fail;
       continue;
     }
     // the ring phase of the first instance (or 0); the others are brought to it (no copies once
@@ -291,17 +295,18 @@ int rfnse_batch_run(rfnse_batch* b, int nsteps, int* iters, double* relres) {
       c->tu_valid[v] = false;
       if (iters) iters[(size_t)s * b->count + i] = pk.it;
       if (relres) relres[(size_t)s * b->count + i] = pk.relres;
-      if (pk.err) {
+      if (pk.err && fail == RFNSE_OK) {
         b->err = "instance " + std::to_string(i) + ": a bounded device-side wait gave up";
-        return RFNSE_ETIMEOUT;
+        fail = RFNSE_ETIMEOUT;
       }
-      if (pk.done == 3) {
+      if (pk.done == 3 && fail == RFNSE_OK) {
         b->err = "instance " + std::to_string(i) + ": non-finite value in the solve";
-        return RFNSE_ENUMERIC;
+        fail = RFNSE_ENUMERIC;
       }
       const bool trivial = pk.beta == 0.0 && pk.it == 0;
       if (!trivial && pk.done != 1 && pk.done != 2) worst = RFNSE_ENOCONV;
     }
+    if (fail != RFNSE_OK) return fail;
   }
   return worst;
 }

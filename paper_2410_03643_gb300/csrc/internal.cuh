@@ -20,6 +20,15 @@ constexpr int kNormPartMax = 4096;  // largest grid whose squared-norm partials 
 extern std::atomic<long long> g_kernel_launches;
 inline void count_launch(long long k = 1) { g_kernel_launches.fetch_add(k, std::memory_order_relaxed); }
 
+// Device and pinned-host allocations of contexts, batches and tapes go through these two (api.cu), so
+// that rfnse_test_fail_allocations can make them fail without exhausting the GPU's memory.
+cudaError_t dev_alloc(void** p, size_t bytes);
+cudaError_t host_alloc_pinned(void** p, size_t bytes);
+
+// Checks of the problem description shared by rfnse_create and rfnse_apply_prec_static: d, grid,
+// box, alpha, rho, dt, omega (api.cu).  Returns null when valid, else the reason.
+const char* validate_problem(const rfnse_params* p);
+
 // Device-resident Arnoldi / Givens state of one GMRES cycle.  H is stored by columns:
 // H(i, j) = H[j * (kMaxM + 1) + i].
 struct GmresState {

@@ -11,7 +11,6 @@
 // calls whose work overlaps on the GPU (different streams, or different host threads) race on the
 // array and give wrong results: serialise them.
 #include <cmath>
-#include <mutex>
 #include "internal.cuh"
 #include "solve.cuh"
 
@@ -19,7 +18,6 @@ namespace {
 
 constexpr long long kStaticMaxN = 1LL << 18;   // largest grid: N = n0*n1*n2 <= 262144 complex values
 constexpr int kStaticMaxL = 4096;              // FFT length 2(n+1) for n + 1 <= 2048
-constexpr int kStaticMaxNAxis = 2047;
 
 // Layout of the array, in double2 units:
 //   [t1: kStaticMaxN][t2: kStaticMaxN][dfac64: kStaticMaxN][lamfac64: kStaticMaxN]
@@ -32,27 +30,15 @@ constexpr long long kStaticElems = 4 * kStaticMaxN + kTableElems;
 
 static __device__ __align__(256) double2 g_prec_scratch[kStaticElems];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_addr_mutex;
-void* g_addr[kMaxDevices] = {};
-
-bool pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
-
 // Device address of g_prec_scratch on the current device.  Host code may not use the symbol itself
-// (it is a host-side stand-in); cudaGetSymbolAddress gives the real address, once per device.
+// (it is a host-side stand-in); cudaGetSymbolAddress gives the real address.  It is looked up on every
+// call rather than cached, so the address stays right after the primary context has been reset and the
+// module reloaded elsewhere in the process.
 cudaError_t scratch_address(double2** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_prec_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_addr_mutex);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_prec_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = p;
-  }
-  *out = static_cast<double2*>(g_addr[dev]);
+  *out = static_cast<double2*>(p);
   return cudaSuccess;
 }
 
@@ -62,15 +48,13 @@ extern "C" int rfnse_apply_prec_static(const rfnse_params* p, const void* v, voi
                                        void* stream) {
   using namespace rfnse;
   if (!p || !v || !z || !D || v == z) return RFNSE_EINVAL;
-  if (p->d < 1 || p->d > 3) return RFNSE_EINVAL;
+  if (validate_problem(p)) return RFNSE_EINVAL;  // the checks of rfnse_create on d, grid, box, alpha, rho, dt, omega
   long long N = 1;
-  for (int a = 0; a < p->d; ++a) {
-    if (p->n[a] < 3 || p->n[a] > kStaticMaxNAxis || !pow2((long long)p->n[a] + 1)) return RFNSE_EINVAL;
-    if (!(p->hi[a] > p->lo[a])) return RFNSE_EINVAL;
-    N *= p->n[a];
-  }
+  for (int a = 0; a < p->d; ++a) N *= p->n[a];
   if (N > kStaticMaxN) return RFNSE_EINVAL;  // larger grids need rfnse_create / rfnse_apply_prec
-  if (!(p->alpha > 1.0 && p->alpha <= 2.0) || !(p->dt > 0.0) || !(p->omega > 0.0)) return RFNSE_EINVAL;
+  // A CUDA error already pending in this thread belongs to the caller: leave it for the caller's own
+  // check and do nothing, so that every error seen below is one this call caused.
+  if (cudaPeekAtLastError() != cudaSuccess) return RFNSE_ECUDA;
 
   double2* base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return RFNSE_ECUDA;
@@ -128,7 +112,7 @@ extern "C" int rfnse_apply_prec_static(const rfnse_params* p, const void* v, voi
   launch_setup_lamfac(c.lam[0], c.lam[1], c.lam[2], c.n[0], c.n[1], c.n[2], hf * c.mu[0], hf * c.mu[1],
                       hf * c.mu[2], p->omega, 1.0 / std::sqrt((double)c.L[c.d - 1]), 0, c.lamfac64[hidx],
                       c.lamfac32[hidx], c.N, c.stream);
-  if (cudaGetLastError() != cudaSuccess) return RFNSE_ECUDA;
+  if (cudaGetLastError() != cudaSuccess) return RFNSE_ECUDA;  // a set-up launch of this call failed
   if (run_apply_prec(&c, (const double2*)v, (double2*)z, D, half ? 1 : 0, 0) != cudaSuccess) return RFNSE_ECUDA;
   if (cudaStreamSynchronize(c.stream) != cudaSuccess) return RFNSE_ECUDA;
   return RFNSE_OK;

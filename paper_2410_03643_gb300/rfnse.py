@@ -57,7 +57,7 @@ EXPORTED = ("rfnse_default_params", "rfnse_create", "rfnse_destroy", "rfnse_last
             "rfnse_profile", "rfnse_profile_read", "rfnse_probe_fma", "rfnse_probe_arnoldi", "rfnse_batch_create",
             "rfnse_batch_destroy", "rfnse_batch_last_error", "rfnse_batch_context", "rfnse_batch_run",
             "rfnse_tape_forward", "rfnse_tape_backward", "rfnse_adjoint_solve", "rfnse_tban_solve",
-            "rfnse_selftest_bounded_wait")
+            "rfnse_selftest_bounded_wait", "rfnse_test_fail_allocations", "rfnse_apply_prec_static")
 
 K_INSCALE, K_DST, K_LAM, K_DSCALE, K_TOEP_X, K_TOEP_ACC, K_FP32, K_DF, K_ARNOLDI = 1, 2, 4, 8, 16, 32, 256, 1024, 2048
 
@@ -132,6 +132,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.rfnse_tban_solve.restype = ip
     lib.rfnse_selftest_bounded_wait.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp]
     lib.rfnse_selftest_bounded_wait.restype = ip
+    lib.rfnse_test_fail_allocations.argtypes = [ctypes.c_longlong]
+    lib.rfnse_test_fail_allocations.restype = ip
     if path == _build.library_path():
         _lib = lib
     return lib
@@ -172,6 +174,12 @@ def selftest_bounded_wait(stream=None):
     if st != RFNSE_OK:
         raise RfnseError(st, "bounded-wait self-test failed to run")
     return err.value, ms.value
+
+
+def fail_allocations_after(after: int) -> None:
+    """After `after` more successful allocations by contexts, batches and tapes, make every later one
+    fail as if the GPU were out of memory (after < 0: no limit, the default)."""
+    load_library().rfnse_test_fail_allocations(int(after))
 
 
 def launch_count() -> int:

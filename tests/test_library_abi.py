@@ -90,3 +90,52 @@ def test_probe_arnoldi_rejects_invalid_arguments_without_gpu_work(libpath):
     for n, j, reps in ((0, 0, 1), (1 << 29, 0, 1), (100, -1, 1), (100, 63, 1), (100, 0, 0), (100, 0, 1001)):
         assert lib.rfnse_probe_arnoldi(n, j, reps, ctypes.byref(us), None) == rfnse.RFNSE_EINVAL
     assert lib.rfnse_probe_arnoldi(100, 0, 1, None, None) == rfnse.RFNSE_EINVAL
+
+
+def test_allocation_failure_is_enomem_without_gpu_work(libpath):
+    """With the allocation hook set to fail at once, rfnse_create reports ENOMEM before any device
+    work, frees what it holds and hands back no context; with the limit removed, invalid parameters are
+    still EINVAL (the hook does not mask validation)."""
+    lib = rfnse.load_library()
+    p = rfnse.Params()
+    lib.rfnse_default_params(ctypes.byref(p))
+    try:
+        assert lib.rfnse_test_fail_allocations(0) == rfnse.RFNSE_OK
+        h = ctypes.c_void_p()
+        assert lib.rfnse_create(ctypes.byref(p), None, ctypes.byref(h)) == rfnse.RFNSE_ENOMEM
+        assert not h.value
+        assert b"allocation" in lib.rfnse_last_error(None)
+    finally:
+        lib.rfnse_test_fail_allocations(-1)
+    p.alpha = 3.0
+    h = ctypes.c_void_p()
+    assert lib.rfnse_create(ctypes.byref(p), None, ctypes.byref(h)) == rfnse.RFNSE_EINVAL
+
+
+def test_static_preconditioner_entry_validates_like_create_without_gpu_work(libpath):
+    """rfnse_apply_prec_static refuses what rfnse_create refuses (non-finite dt, omega, rho or box) and
+    grids beyond its static array, before any device call; the pointers are never dereferenced."""
+    lib = rfnse.load_library()
+    lib.rfnse_apply_prec_static.argtypes = [ctypes.POINTER(rfnse.Params), ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    lib.rfnse_apply_prec_static.restype = ctypes.c_int
+    inf, nan = float("inf"), float("nan")
+    cases = []
+    for field, value in (("dt", inf), ("dt", nan), ("omega", inf), ("rho", inf), ("rho", -1.0), ("alpha", nan),
+                         ("d", 0)):
+        p = rfnse.Params()
+        lib.rfnse_default_params(ctypes.byref(p))
+        setattr(p, field, value)
+        cases.append(p)
+    p = rfnse.Params()
+    lib.rfnse_default_params(ctypes.byref(p))
+    p.hi[0] = inf
+    cases.append(p)
+    p = rfnse.Params()                      # N = 1023 * 511 > 262144: beyond the static array
+    lib.rfnse_default_params(ctypes.byref(p))
+    p.d, p.n[0], p.n[1] = 2, 1023, 511
+    cases.append(p)
+    dummy = ctypes.c_void_p(0x1000)
+    for p in cases:
+        assert lib.rfnse_apply_prec_static(ctypes.byref(p), dummy, ctypes.c_void_p(0x2000), dummy, 0,
+                                           None) == rfnse.RFNSE_EINVAL

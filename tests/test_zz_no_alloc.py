@@ -45,6 +45,11 @@ CASES = [
     (W.config_2d(1.5)[0], False),                                                       # 511 x 511, the maximum size
     (W.Problem(d=3, n=(15, 7, 31), lo=(-4.0, -3.0, -5.0), hi=(4.0, 3.0, 5.0), alpha=1.3, rho=1.0, dt=0.01), True),
     (W.Problem(d=1, n=(1023,), lo=(-20.0,), hi=(20.0,), alpha=1.9, rho=2.0, dt=0.01), False),
+    # the largest axis the array's table slots hold (n = 2047, FFT length 4096) on the first axis, and
+    # the smallest on the other two: every axis's table slot is written, both time levels
+    (W.Problem(d=3, n=(2047, 3, 3), lo=(-20.0, -1.0, -2.0), hi=(20.0, 1.0, 2.0), alpha=1.6, rho=1.0, dt=0.01), False),
+    (W.Problem(d=3, n=(2047, 3, 3), lo=(-20.0, -1.0, -2.0), hi=(20.0, 1.0, 2.0), alpha=1.6, rho=1.0, dt=0.01), True),
+    (W.Problem(d=3, n=(3, 2047, 3), lo=(-1.0, -20.0, -2.0), hi=(1.0, 20.0, 2.0), alpha=1.2, rho=1.0, dt=0.01), True),
 ]
 
 
