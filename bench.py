@@ -12,11 +12,16 @@ beside it, with the difference between the two trajectories.  DOF = complex grid
                   [--workload 2d|3d|1d|batched|adjoint|comparators|omega] [--instances K]
   python bench.py --alu-probe | --arnoldi-probe
 
-The JSON line's roofline objects are the three largest kernel classes of the step, each timed launch
-by launch (CUDA events) in a further serial run with host-driven loops: the cooperative Arnoldi
-kernel, the FP32 fused x-pass and the double-float residual x-pass.  --instances K runs K 511^2
-instances instead of three (the throughput saturates from about 6 on); --arnoldi-probe times the
-Arnoldi kernel alone per column j; --alu-probe measures the FP64 and FP32 FMA rates.
+The metric names two halves, and the default line carries both: the 2-D workload above (the line's
+own value) and, under "config_3d", the 3-D workload (n = 255^3 on [-8,8]^3, alpha = 1.7, rho = 1,
+dt = 0.01, u0 = exp(-|x|^2/2)e^{ix_1}, tol 1e-8), each with the FP64 form beside the mixed one, the
+per-step error of both forms against the CPU oracle's trajectory from the same u^0 ("err_vs_oracle"),
+an end-to-end figure with host buffers ("e2e") and the oracle's own throughput on the host cores, all
+cores and (2-D) one core ("cpu_baseline").  The roofline objects are the three largest kernel classes
+of each workload's step, every class timed launch by launch (CUDA events) in a further serial run
+with host-driven loops.  --instances K runs K 511^2 instances instead of three (the throughput
+saturates from about 6 on); --no-3d leaves the 3-D half out; --arnoldi-probe times the Arnoldi kernel
+alone per column j; --alu-probe measures the FP64 and FP32 FMA rates.
 
 Other workloads: 3d (255^3, mixed), 1d (n = 1023), batched (64 independent 2-D instances with grids
 drawn from {127, 255, 511}^2: one step = one graph launch advancing all of them), adjoint (255^2,
@@ -51,9 +56,8 @@ import workloads as W  # noqa: E402
 METRIC = "DOF*timesteps/s"
 UNIT = "DOF*timesteps/s"
 FP64_ALU_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the FP64 Toeplitz x-pass (ncu)
-TRAFFIC_FP64_TOEP_X = {"2d": 10530816 + 0}
 FP32_ALU_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9  # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
+CSRC = os.path.join(ROOT, "paper_2410_03643_gb300", "csrc")
 
 
 def measured_hbm_gbs():
@@ -65,15 +69,61 @@ def measured_hbm_gbs():
         return 6800.0, "fallback"
 
 
-# DRAM read+write per launch of the FP32 fused DST-x + (wI+D) + Toeplitz-x pass (ncu, 2-D 511^2,
-# k_line_pass_fixed<float2, float2, double2, float2, 26, 10>)
-TRAFFIC_FP32_FUSED_X = {"2d": 5288960 + 0}
-# DRAM read+write per launch of the cooperative Arnoldi kernel (ncu, 2-D 511^2: mean of 10 consecutive
-# launches, columns j = 1,0,1,2,0,1,0,1,2,0, the mix of the bench's solves; (j + 2) x 4.2 MB each)
-TRAFFIC_ARNOLDI = {"2d": 11744538 + 0}
-# DRAM read+write per launch of the double-float residual x-pass (ncu, 2-D 511^2, steady launch: the
-# launches alternate 6.36 / 10.54 MB, the larger after the first step's extra product)
-TRAFFIC_DF_TOEP_X = {"2d": 6360320 + 0}
+# Kernel classes timed launch by launch for the roofline objects: rfnse_profile kind (OR of the pass
+# flags, +256 for FP32 passes, +1024 for the double-float residual passes, 2048 for the Arnoldi kernel),
+# the roofline that bounds the class, its description, and the sources its kernels are compiled from.
+_PASS_SRC = ("passes.cuh", "fft_fixed.cuh", "fft_line.cuh", "cplx.cuh")
+_DF_SRC = ("toep_df.cu", "dfloat.cuh", "fft_fixed.cuh", "cplx.cuh")
+KERNEL_CLASSES = {
+    "arnoldi": (2048, "alu", "k_mgs_step (cooperative MGS + Givens + convergence test, one launch per Arnoldi "
+                             "step)", ("control.cu",)),
+    "fp32_fused_x": (256 | 2 | 8 | 16, "hbm", "line pass <float, F_DST|F_DSCALE|F_TOEP_X> (inverse DST x + "
+                                              "(wI+D) sub-solve + Toeplitz x)", _PASS_SRC),
+    "fp32_dst": (256 | 2, "hbm", "line pass <float, F_DST> (DST x with the Arnoldi scaling folded in; DST y in 3-D)",
+                 _PASS_SRC),
+    "fp32_dst_lam": (256 | 2 | 4, "hbm", "line pass <float, F_DST|F_LAM> (DST, divide by (w + i Lambda), DST; last "
+                                         "axis)", _PASS_SRC),
+    "fp32_toep_acc": (256 | 32, "hbm", "line pass <float, F_TOEP_ACC> (Toeplitz y / z, accumulated)", _PASS_SRC),
+    "fp32_all_1d": (256 | 2 | 4 | 8 | 16, "hbm", "line pass <float, all flags> (1-D preconditioner + product)",
+                    _PASS_SRC),
+    "df_toep_x": (1024 | 16, "hbm", "k_toeplitz_df<F_TOEP_X> (residual Toeplitz x, double-float FFTs)", _DF_SRC),
+    "df_toep_acc": (1024 | 32, "hbm", "k_toeplitz_df<F_TOEP_ACC> (residual Toeplitz y / z, double-float FFTs)",
+                    _DF_SRC),
+}
+PROFILED = {
+    "2d": ("arnoldi", "fp32_fused_x", "fp32_dst", "fp32_dst_lam", "fp32_toep_acc", "df_toep_x", "df_toep_acc"),
+    "3d": ("arnoldi", "fp32_fused_x", "fp32_dst", "fp32_dst_lam", "fp32_toep_acc", "df_toep_x", "df_toep_acc"),
+    "1d": ("arnoldi", "fp32_all_1d", "df_toep_x"),
+}
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch (ncu, one capture each) of a class on a
+# workload, with the digest of the class's sources when it was taken: once a source has changed the
+# figure no longer describes the kernel and the line reports traffic null.
+TRAFFIC = {
+    ("2d", "arnoldi"): (11744538, "dfc6e2f299f1"),
+    ("2d", "fp32_fused_x"): (5288960, "aa1b09e3a567"),
+    ("2d", "df_toep_x"): (6360320, "344a18e48fe5"),
+}
+
+
+def source_digest(files) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def traffic_for(workload_name: str, cls: str):
+    """(bytes per launch or None, note)."""
+    rec = TRAFFIC.get((workload_name, cls))
+    if rec is None:
+        return None, "no ncu capture of this class on this workload"
+    value, digest = rec
+    if digest != source_digest(KERNEL_CLASSES[cls][3]):
+        return None, "stale: the kernel's sources changed since the ncu capture"
+    return value, "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch"
 
 
 def parse():
@@ -94,6 +144,16 @@ def parse():
     ap.add_argument("--arnoldi-probe", action="store_true",
                     help="only time the cooperative Arnoldi kernel (MGS + Givens) per column j on the 2-D and "
                          "3-D grid sizes and print the times")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch geometry of the line passes")
+    ap.add_argument("--no-3d", action="store_true",
+                    help="default 2d workload: leave out the 3-D 255^3 half of the metric (config_3d)")
+    ap.add_argument("--kernel-case", default=None, choices=["2d", "3d"],
+                    help="only run a small case for kernel profilers: one mixed solve of the workload's grid "
+                         "with host-driven loops, restart 2 and at most 4 Arnoldi steps (a 255^3 case holds "
+                         "about 4 GB on the device), then exit")
+    ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-steps", type=int, default=2, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-state", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--instances", type=int, default=3,
                     help="2d workload: number of 511^2 instances advanced together (alphas cycle through "
                          "1.2, 1.5, 1.9); the default 3 is the headline configuration")
@@ -221,19 +281,21 @@ def barrier(world: int):
 
 # --- the CPU oracle as the baseline / reference arm ---------------------------------------------
 def oracle_sample(inst, nsteps: int):
-    """Time `nsteps` regular time steps (n >= 1) of the first instance with the CPU oracle.
-    Returns (DOF x steps / s, seconds, steps)."""
+    """The first `nsteps` + 1 steps of the first instance with the CPU oracle, timing the `nsteps`
+    regular steps (n >= 1).  Returns (DOF x steps / s, seconds, steps, [u^1 .. u^{nsteps+1}])."""
     from oracle.scheme import SchemeOracle
     p, u0 = inst[0]
     o = SchemeOracle(p)
     u1, _, _ = o.first_step(u0)
+    traj = [u1]
     up, uc = u0, u1
     t0 = time.perf_counter()
     for _ in range(nsteps):
         un, _, _ = o.step(up, uc)
+        traj.append(un)
         up, uc = uc, un
     dt = time.perf_counter() - t0
-    return p.size * nsteps / dt, dt, nsteps
+    return p.size * nsteps / dt, dt, nsteps, traj
 
 
 def host_cores() -> int:
@@ -241,6 +303,58 @@ def host_cores() -> int:
         return len(os.sched_getaffinity(0))
     except AttributeError:
         return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_sample_child(args):
+    """Child of oracle_single_thread: time args.cpu_steps regular oracle steps from the state in
+    args.cpu_state (BLAS limited to one thread by the parent's environment) and print one JSON line."""
+    from oracle.scheme import SchemeOracle
+    inst, _ = workload(args.cpu_sample, 1)
+    p = inst[0][0]
+    z = np.load(args.cpu_state)
+    up, uc = z["u_prev"], z["u_cur"]
+    o = SchemeOracle(p)
+    t0 = time.perf_counter()
+    for _ in range(args.cpu_steps):
+        un, _, _ = o.step(up, uc)
+        up, uc = uc, un
+    dt = time.perf_counter() - t0
+    print(json.dumps({"value": p.size * args.cpu_steps / dt, "seconds": dt, "steps": args.cpu_steps}), flush=True)
+
+
+def oracle_single_thread(name: str, u_prev, u_cur, steps: int):
+    """The oracle on one host core: a child process with every BLAS / OpenMP pool set to one thread,
+    timing `steps` regular steps from (u_prev, u_cur).  Returns its JSON record or None."""
+    import tempfile
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+              "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "state.npz")
+        np.savez(path, u_prev=u_prev, u_cur=u_cur)
+        try:
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", name, "--cpu-steps",
+                                str(steps), "--cpu-state", path], env=env, capture_output=True, text=True,
+                               timeout=900)
+        except subprocess.SubprocessError:
+            return None
+    for line in reversed(r.stdout.splitlines()):
+        if line.startswith("{"):
+            return json.loads(line)
+    return None
 
 
 def run_reference(args):
@@ -280,36 +394,87 @@ def run_reference(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (closed-form initial data of the paper's shape)",
            "config": dict(desc, sample="one time step of one alpha instance per bench step"),
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                             "sample": f"{args.steps} time steps, instances in turn, numpy/BLAS on {cores} host cores"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
 # --- our CUDA path --------------------------------------------------------------------------------
-def run_ours(args):
-    import torch
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-    from paper_2410_03643_gb300 import build, rfnse
-    build.build_library()
-    inst, desc = workload(args.workload, args.instances)
-    main = torch.cuda.current_stream()
+class Env:
+    """What every measurement of the CUDA path shares: torch, the binding, the device and stream, the
+    rank layout and the L2-flush buffer."""
+
+    def __init__(self, torch, rfnse, dev, main, rank, world, local):
+        self.torch, self.rfnse, self.dev, self.main = torch, rfnse, dev, main
+        self.rank, self.world, self.local = rank, world, local
+        self.flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+
+def roofline_entry(name: str, cls: str, prof, ms_serial: float, nprof: int):
+    """The roofline object of one kernel class from its launch-by-launch profile (launches, ms,
+    algorithmic flops, algorithmic bytes)."""
+    n, pms, fl, by = prof
+    kind, bound, desc, _ = KERNEL_CLASSES[cls]
+    hbm, how = measured_hbm_gbs()
+    traffic, tnote = traffic_for(name, cls)
+    gbs = by / (pms * 1e-3) / 1e9
+    e = {"class": cls, "kernel": desc, "launches": n, "avg_launch_us": 1e3 * pms / n, "total_ms": pms,
+         "share_of_step_time": pms / ms_serial if ms_serial > 0 else None,
+         "measured": f"CUDA events around every launch of the class (on its stream), serial run of {nprof} "
+                     "further bench steps with host-driven loops (the kernels of the graphs)",
+         "algorithmic_flops_per_launch": fl / n, "algorithmic_bytes_per_launch": by / n,
+         "traffic": (traffic / 1.0) if traffic is not None else None, "traffic_note": tnote}
+    if bound == "alu":
+        achieved = fl / (pms * 1e-3) / 1e12
+        e.update({"bound": "alu", "achieved": achieved, "peak": FP64_ALU_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                  "frac": achieved * 1e12 / FP64_ALU_PEAK_FLOPS, "achieved_GBs": gbs, "frac_of_hbm": gbs / hbm,
+                  "peak_note": "FP64 FMA issue rate: 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz = 1.26 TFLOP/s "
+                               "(bench.py --alu-probe measures it); the algorithmic FP64 flops per launch "
+                               "(8 (j + 1) + 4 per point) need more time at that rate than its bytes at the "
+                               f"copy bandwidth ({how}, beside it)"})
+    else:
+        e.update({"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                  "achieved_TFLOPs": fl / (pms * 1e-3) / 1e12,
+                  "peak_note": f"copy bandwidth, {how} (MEASURED_PEAKS.json); algorithmic bytes = every "
+                               "operand read once and every result written once"})
+        if cls.startswith("df_"):
+            e["fp64_equivalent_frac_of_fp64_alu_peak"] = fl / (pms * 1e-3) / FP64_ALU_PEAK_FLOPS
+        else:
+            e["frac_of_fp32_alu_peak"] = fl / (pms * 1e-3) / FP32_ALU_PEAK_FLOPS
+    return e
+
+
+def rel_errors(got, want):
+    return [float(np.linalg.norm((g - w).ravel()) / np.linalg.norm(w.ravel())) for g, w in zip(got, want)]
+
+
+def measure(args, env: Env, name: str, instances: int, steps: int, warmup: int, oracle_steps: int,
+            single_thread_steps: int, e2e_steps: int):
+    """One workload through the CUDA path: the mixed form timed (the value), its largest kernel classes
+    launch by launch (roofline objects), the FP64 form timed the same way, the per-step error of both
+    forms against the CPU oracle, the end-to-end figure through the C ABI with host buffers, and the
+    oracle's own throughput on the host cores.  Returns the JSON record."""
+    torch, rfnse, dev, main, world, rank = env.torch, env.rfnse, env.dev, env.main, env.world, env.rank
+    inst, desc = workload(name, instances)
     concurrent = not args.serial and len(inst) > 1
     pool = ThreadPoolExecutor(max_workers=len(inst)) if concurrent else None
     # several instances advance together through the batch API (one graph launch per step for all);
     # host-driven loops (--host-loop, for kernel profilers) keep one host thread per instance
     use_batch = concurrent and not args.host_loop
 
+    tuning = {}
+
     def make(precision, device_loop=None, batch=None):
+        """The instances in one precision; their line passes autotuned (each grid is timed once per
+        process, later contexts reuse the choice) unless --no-autotune."""
         if device_loop is None:
             device_loop = 0 if args.host_loop else 1
         if use_batch if batch is None else batch:
             b = rfnse.Batch([p for p, _ in inst], precision=precision, stream=main, device_loop=device_loop)
+            if not args.no_autotune:
+                nc, ch = b.autotune(reps=5)
+                tuning.setdefault(precision, {"configs": nc, "changed": ch})
             for i, (p, u0) in enumerate(inst):
                 b.set_state(i, torch.from_numpy(u0.ravel().copy()).to(dev))
             torch.cuda.synchronize()
@@ -318,6 +483,9 @@ def run_ours(args):
         for p, u0 in inst:
             st = torch.cuda.Stream(device=dev) if concurrent else main
             s = rfnse.Solver(p, precision=precision, stream=st, device_loop=device_loop)
+            if not args.no_autotune:
+                nc, ch, sp = s.autotune(reps=5)
+                tuning.setdefault(precision, {"configs": nc, "changed": ch, "est_speedup": sp})
             s.set_state(torch.from_numpy(u0.ravel().copy()).to(dev))
             solvers.append(s)
         torch.cuda.synchronize()
@@ -351,31 +519,28 @@ def run_ours(args):
             for s in group:
                 s.close()
 
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     dof_per_step = sum(p.size for p, _ in inst)
 
-    def timed(solvers, steps, warmup, profile_kind=0, clocks=None, serial=False):
-        for _ in range(warmup):
+    def timed(solvers, nsteps, nwarm, profile_kind=0, clocks=None, serial=False):
+        for _ in range(nwarm):
             advance(solvers, serial=serial)
         torch.cuda.synchronize()
         if profile_kind:
             for s in solvers:
                 s.profile(profile_kind)
         launches0 = rfnse.launch_count()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
         iters = []
         barrier(world)
         torch.cuda.synchronize()
         if clocks:
             clocks.mark_on()
-        wall0 = time.perf_counter()
-        for k in range(steps):
-            flush.fill_(float(k))                       # evict L2 between timed steps
+        for k in range(nsteps):
+            env.flush.fill_(float(k))                   # evict L2 between timed steps
             evs[k][0].record(main)
             iters += advance(solvers, evs[k][0], serial=serial)
             evs[k][1].record(main)
         torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
         if clocks:
             clocks.mark_off()
         barrier(world)
@@ -389,50 +554,21 @@ def run_ours(args):
                 tot[0] += n; tot[1] += pms; tot[2] += fl; tot[3] += by
                 s.profile(0)
             prof = tot
-        return ms, wall, launches, iters, prof
+        return ms, launches, iters, prof
 
     # headline: mixed form
     mixed = make(1)
-    clocks = ClockSampler(local) if rank == 0 else None
+    clocks = ClockSampler(env.local) if rank == 0 else None
     if clocks:
         clocks.start()
-    # the residual's Toeplitz pass along x (double-float FFTs in the mixed form on these grids); for 1-D
-    # the preconditioner and the product share one FP32 pass
-    dom_kind = (rfnse.K_DF | rfnse.K_TOEP_X) if args.workload != "1d" else \
-        (rfnse.K_FP32 | rfnse.K_DST | rfnse.K_LAM | rfnse.K_DSCALE | rfnse.K_TOEP_X)
-    ms, wall, launches, iters_m, _ = timed(mixed, args.steps, args.warmup, clocks=clocks)
+    ms, launches, iters_m, _ = timed(mixed, steps, warmup, clocks=clocks)
     clk = clocks.stop() if clocks else None
     mixed_states = states_of(mixed)   # after warmup + steps, for the FP64 comparison
-    # the dominant kernel class, timed launch by launch in a further serial run of the same steps
-    # (in the concurrent region the instances' kernels share the SMs, which stretches each launch)
-    # (host-driven solvers: CUDA events cannot be recorded around single kernels inside a running graph;
-    # the kernels are the same as in the device loop)
-    nprof = max(1, min(args.steps, 20))
-    prof_solvers = make(1, device_loop=0, batch=False)
-    ms_r, _, _, _, prof = timed(prof_solvers, nprof, args.warmup, profile_kind=dom_kind, serial=True)
-    for s in prof_solvers:
-        s.close()
-    # the other large class: the FP32 pass that ends the preconditioner and starts the product along x
-    prof32 = None
-    if args.workload in ("2d", "3d"):
-        k32 = rfnse.K_FP32 | rfnse.K_DST | rfnse.K_DSCALE | rfnse.K_TOEP_X
-        prof_solvers = make(1, device_loop=0, batch=False)
-        ms_r32, _, _, _, prof32 = timed(prof_solvers, nprof, args.warmup, profile_kind=k32, serial=True)
-        for s in prof_solvers:
-            s.close()
-    # the cooperative Arnoldi kernel (MGS, Givens, test), launched on its own by the host-driven loops
-    prof_arn = None
-    if args.workload in ("2d", "3d"):
-        prof_solvers = make(1, device_loop=0, batch=False)
-        ms_ra, _, _, _, prof_arn = timed(prof_solvers, nprof, args.warmup, profile_kind=rfnse.K_ARNOLDI, serial=True)
-        for s in prof_solvers:
-            s.close()
+    close_all(mixed)
     ms_max = reduce_max(ms, world, dev)
-    value = weak_value(world, dof_per_step, args.steps, ms_max)
-
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
+    out = {"metric": METRIC, "value": weak_value(world, dof_per_step, steps, ms_max), "unit": UNIT,
+           "n_gpus": world, "steps": steps, "warmup": warmup, "ms_per_step": ms_max / steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
            "data": "synthetic (closed-form initial data of the paper's shape)",
            "config": dict(desc, precision="mixed: FP32 transforms in FGMRES, FP64 Arnoldi/Givens/residual",
                           l2="256 MiB buffer written between timed steps",
@@ -445,99 +581,49 @@ def run_ours(args):
                                    else "device-decided GMRES loops, one CUDA graph per solve")),
            "gpu_launches": launches,
            "iters_per_solve_mean": float(np.mean(iters_m)) if iters_m else None}
-
-    # roofline of the two largest kernel classes, each timed launch by launch; the larger is `roofline`
-    measured = ("CUDA events around every launch of the class (on its stream), serial run of "
-                f"{nprof} further bench steps")
-    entries = []
-    if prof and prof[0] > 0 and args.workload != "1d":
-        n, pms, fl, by = prof
-        hbm, how = measured_hbm_gbs()
-        achieved = by / (pms * 1e-3) / 1e9
-        fp64eq = fl / (pms * 1e-3) / 1e12
-        entries.append({"bound": "hbm", "kernel": "k_toeplitz_df<F_TOEP_X> (residual Toeplitz x-pass, "
-                                                  "double-float FFTs)",
-                        "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                        # profiles/k_toeplitz_df_x_2d511.md
-                        "traffic": TRAFFIC_DF_TOEP_X.get(args.workload), "launches": n,
-                        "avg_launch_us": 1e3 * pms / n, "total_ms": pms,
-                        "share_of_step_time": pms / ms_r if ms_r > 0 else None, "measured": measured,
-                        "algorithmic_flops_per_launch": fl / n, "algorithmic_bytes_per_launch": by / n,
-                        "fp64_equivalent_TFLOPs": fp64eq,
-                        "frac_of_fp64_alu_peak": fp64eq * 1e12 / FP64_ALU_PEAK_FLOPS,
-                        "peak_note": f"copy bandwidth, {how} (MEASURED_PEAKS.json).  The FFTs run in "
-                                     "double-float on the FP32 pipes, so their FP64-accurate flop rate may "
-                                     "exceed the native FP64 peak (152 SM x 2 FMA/clk x 2 x 2.07 GHz)"})
-    if prof and prof[0] > 0 and args.workload == "1d":
-        n, pms, fl, by = prof
-        hbm, how = measured_hbm_gbs()
-        achieved = by / (pms * 1e-3) / 1e9
-        entries.append({"bound": "hbm", "kernel": "k_line_pass<float,all flags> (1-D FP32 preconditioner + "
-                                                  "product)", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                        "frac": achieved / hbm, "traffic": None, "launches": n, "avg_launch_us": 1e3 * pms / n,
-                        "total_ms": pms, "share_of_step_time": pms / ms_r if ms_r > 0 else None,
-                        "measured": measured, "peak_note": f"copy bandwidth, {how}"})
-    if prof32 and prof32[0] > 0:
-        n, pms, fl, by = prof32
-        hbm, how = measured_hbm_gbs()
-        achieved = by / (pms * 1e-3) / 1e9
-        entries.append({"bound": "hbm", "kernel": ("k_line_pass_fixed" if args.workload == "2d" else "k_line_pass")
-                                                  + "<float,F_DST|F_DSCALE|F_TOEP_X> "
-                                                  "(FP32 inverse DST x + (wI+D) + Toeplitz x)",
-                        "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                        # profiles/k_line_pass_fp32_fused_x_2d511.md
-                        "traffic": TRAFFIC_FP32_FUSED_X.get(args.workload), "launches": n,
-                        "avg_launch_us": 1e3 * pms / n, "total_ms": pms,
-                        "share_of_step_time": pms / ms_r32 if ms_r32 > 0 else None, "measured": measured,
-                        "algorithmic_flops_per_launch": fl / n, "algorithmic_bytes_per_launch": by / n,
-                        "achieved_TFLOPs": fl / (pms * 1e-3) / 1e12,
-                        "frac_of_fp32_alu_peak": fl / (pms * 1e-3) / FP32_ALU_PEAK_FLOPS,
-                        "peak_note": f"copy bandwidth, {how} (MEASURED_PEAKS.json); arithmetic intensity "
-                                     f"{fl / by:.1f} flop/B is below the FP32 balance point"})
-    if prof_arn and prof_arn[0] > 0:
-        n, pms, fl, by = prof_arn
-        hbm, how = measured_hbm_gbs()
-        achieved = fl / (pms * 1e-3) / 1e12
-        entries.append({"bound": "alu", "kernel": "k_mgs_step (cooperative MGS + Givens + convergence test, "
-                                                  "one launch per Arnoldi step)",
-                        "achieved": achieved, "peak": FP64_ALU_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-                        "frac": achieved * 1e12 / FP64_ALU_PEAK_FLOPS,
-                        # profiles/k_mgs_step_2d511.md
-                        "traffic": TRAFFIC_ARNOLDI.get(args.workload), "launches": n,
-                        "avg_launch_us": 1e3 * pms / n, "total_ms": pms,
-                        "share_of_step_time": pms / ms_ra if ms_ra > 0 else None, "measured": measured,
-                        "algorithmic_flops_per_launch": fl / n, "algorithmic_bytes_per_launch": by / n,
-                        "achieved_GBs": by / (pms * 1e-3) / 1e9, "frac_of_hbm": by / (pms * 1e-3) / 1e9 / hbm,
-                        "peak_note": "FP64 FMA issue rate, 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz (1.26 TFLOP/s "
-                                     "measured by --alu-probe); the kernel performs j + 2 sweeps with a grid-wide "
-                                     "reduction after each, and the synchronisation between sweeps, not the FP64 "
-                                     f"pipe or memory, sets its time ({how} copy bandwidth beside it)"})
-    if entries:
-        entries.sort(key=lambda e: -e["total_ms"])
-        out["roofline"] = entries[0]
-        if len(entries) > 1:
-            out["roofline_second"] = entries[1]
-        if len(entries) > 2:
-            out["roofline_third"] = entries[2]
     if clk:
         out["clocks"] = clk
+    out["autotune"] = ({"mixed": tuning.get(1), "what": "rfnse_autotune: lines per block, FFT threads per line "
+                        "and kernel variant of every line-pass configuration, chosen by timing (set-up, not timed)"}
+                       if not args.no_autotune else None)
+
+    # the largest kernel classes, each timed launch by launch in a further serial run of the same steps
+    # with host-driven loops (CUDA events cannot be placed around single kernels inside a running graph;
+    # the kernels are the same); in the concurrent region the instances share the SMs, which stretches
+    # each launch, so the serial run gives the kernels' own durations
+    nprof = max(1, min(steps, 20))
+    entries = []
+    for cls in PROFILED.get(name, ()):
+        prof_solvers = make(1, device_loop=0, batch=False)
+        ms_r, _, _, prof = timed(prof_solvers, nprof, min(warmup, 3), profile_kind=KERNEL_CLASSES[cls][0],
+                                 serial=True)
+        close_all(prof_solvers)
+        if prof and prof[0] > 0:
+            entries.append(roofline_entry(name, cls, prof, ms_r, nprof))
+    entries.sort(key=lambda e: -e["total_ms"])
+    for key, e in zip(("roofline", "roofline_second", "roofline_third"), entries):
+        out[key] = e
+    if entries:
+        out["kernel_classes"] = {e["class"]: {"share_of_step_time": e["share_of_step_time"],
+                                              "avg_launch_us": e["avg_launch_us"], "frac": e["frac"],
+                                              "bound": e["bound"]} for e in entries}
 
     # plain FP64 form, same protocol, and the distance between the two trajectories
     if not args.no_fp64:
         fp64 = make(0)
-        ms64, _, _, iters64, _ = timed(fp64, args.steps, args.warmup)
+        ms64, _, iters64, _ = timed(fp64, steps, warmup)
         ms64 = reduce_max(ms64, world, dev)
-        errs = []
-        for ua, ub in zip(mixed_states, states_of(fp64)):
-            errs.append(float(torch.linalg.vector_norm(ua - ub) / torch.linalg.vector_norm(ub)))
-        out["fp64"] = {"value": world * dof_per_step * args.steps / (ms64 * 1e-3), "ms_per_step": ms64 / args.steps,
+        errs = [float(torch.linalg.vector_norm(ua - ub) / torch.linalg.vector_norm(ub))
+                for ua, ub in zip(mixed_states, states_of(fp64))]
+        out["fp64"] = {"value": weak_value(world, dof_per_step, steps, ms64), "ms_per_step": ms64 / steps,
                        "iters_per_solve_mean": float(np.mean(iters64)) if iters64 else None}
         out["mixed_vs_fp64_rel_l2_after_run"] = max(errs)
         out["mixed_speedup_vs_fp64"] = ms64 / ms_max
         close_all(fp64)
+    del mixed_states
 
     # end to end through the C ABI with host buffers: H2D of the step's inputs, D2H of its result
-    if not args.no_e2e:
+    if not args.no_e2e and e2e_steps > 0:
         e2e_solvers = make(1, batch=False)
         for s in e2e_solvers:
             s.run(2)  # reach a regular step
@@ -550,17 +636,17 @@ def run_ours(args):
             pin_up.copy_(up.cpu())
             pin_uc.copy_(uc.cpu())
             hosts.append([pin_up, pin_uc, pin_out, step])
-        steps_e2e = max(1, min(args.steps, 30))
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()
+
         def e2e_one(s, h):
             s.set_state_host(h[1].numpy(), h[0].numpy(), h[3])     # H2D of u^{n-1}, u^n
             s.run_host(1, h[2].numpy())                            # step + D2H of u^{n+1}
             h[0], h[1], h[2] = h[1], h[2], h[0]
             h[3] += 1
 
-        for _ in range(steps_e2e):
+        for _ in range(e2e_steps):
             if concurrent:
                 for f in [pool.submit(e2e_one, s, h) for s, h in zip(e2e_solvers, hosts)]:
                     f.result()
@@ -570,19 +656,72 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_s = reduce_max(time.perf_counter() - t0, world, dev)
         nb = sum(s.N for s in e2e_solvers) * 16
-        out["e2e"] = {"value": world * dof_per_step * steps_e2e / e2e_s, "unit": UNIT,
-                      "h2d_bytes_per_step": 2 * nb, "d2h_bytes_per_step": nb, "steps": steps_e2e}
-        for s in e2e_solvers:
-            s.close()
+        out["e2e"] = {"value": weak_value(world, dof_per_step, e2e_steps, 1e3 * e2e_s), "unit": UNIT,
+                      "h2d_bytes_per_step": 2 * nb, "d2h_bytes_per_step": nb, "steps": e2e_steps}
+        close_all(e2e_solvers)
+        del hosts
 
-    # the CPU oracle on the host cores (bounded sample), rank 0 at N = 1 only
-    if not args.no_cpu and rank == 0 and world == 1:
-        n_cpu = 30 if args.workload != "3d" else 1
-        v, secs, n = oracle_sample(inst, n_cpu)
-        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
-                               "sample": f"{n} time steps of the alpha={inst[0][0].alpha} instance "
-                                         f"({secs:.1f} s), numpy/BLAS dense-transform oracle"}
-    close_all(mixed)
+    # the CPU oracle on the host cores (bounded sample) and the per-step error of both GPU forms against
+    # the oracle's trajectory of the first instance (rank 0 at N = 1 only)
+    if not args.no_cpu and rank == 0 and world == 1 and oracle_steps > 0:
+        v, secs, n, otraj = oracle_sample(inst, oracle_steps)
+        p0, u00 = inst[0]
+        cores = host_cores()
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+                               "sample": f"{n} regular time steps of the alpha={p0.alpha} instance ({secs:.1f} s) "
+                                         f"after its first step, numpy/BLAS dense-transform oracle on {cores} "
+                                         "host cores"}
+        if single_thread_steps > 0 and len(otraj) >= 2:
+            st1 = oracle_single_thread(name, otraj[-2], otraj[-1], single_thread_steps)
+            if st1:
+                out["cpu_baseline"]["single_thread"] = {
+                    "value": st1["value"], "unit": UNIT, "cores": 1,
+                    "sample": f"{st1['steps']} regular time steps of the same instance ({st1['seconds']:.1f} s), "
+                              "BLAS and OpenMP pools set to one thread"}
+        nk = len(otraj)
+        errs = {}
+        for precision, label in ((1, "mixed"), (0, "fp64")):
+            s = rfnse.Solver(p0, precision=precision, stream=main)
+            s.set_state(torch.from_numpy(u00.ravel().copy()).to(dev))
+            gt = torch.empty(nk * p0.size, dtype=torch.complex128, device=dev)
+            s.run(nk, gt)
+            g = gt.cpu().numpy().reshape((nk,) + p0.shape)
+            s.close()
+            del gt
+            e = rel_errors(g, otraj)
+            errs[label] = {"steps": nk, "max": max(e), "last": e[-1],
+                           "per_step": [float(f"{x:.3g}") for x in e]}
+            del g
+        out["err_vs_oracle"] = dict(errs, what=f"relative L2 error of u^1..u^{nk} of the alpha={p0.alpha} instance "
+                                               "against the FP64 CPU oracle's trajectory from the same u^0",
+                                    tol=p0.tol)
+    return out
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2410_03643_gb300 import build, rfnse
+    build.build_library()
+    env = Env(torch, rfnse, dev, torch.cuda.current_stream(), rank, world, local)
+    headline = args.workload == "2d" and args.instances == 3
+    out = measure(args, env, args.workload, args.instances, args.steps, args.warmup,
+                  oracle_steps=30 if args.workload in ("2d", "1d") else 1,
+                  single_thread_steps=2 if args.workload in ("2d", "1d") else 0,
+                  e2e_steps=max(1, min(args.steps, 30 if args.workload != "3d" else 10)))
+    # the metric names both halves: the default line also carries the 3-D 255^3 workload, measured the
+    # same way (its oracle sample is the first step and one regular step)
+    if headline and not args.no_3d:
+        sub = measure(args, env, "3d", 1, args.steps, args.warmup, oracle_steps=1, single_thread_steps=0,
+                      e2e_steps=max(1, min(args.steps, 10)))
+        for k in ("metric", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "data"):
+            sub.pop(k, None)
+        out["config_3d"] = sub
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -608,6 +747,8 @@ def run_batched(args):
 
     def timed(precision, clocks=None):
         b = rfnse.Batch([p for p, _ in inst], precision=precision, stream=main)
+        if not args.no_autotune:
+            b.autotune(reps=5)                      # every distinct grid timed once (set-up, not timed)
         for i, (p, u0) in enumerate(inst):
             b.set_state(i, torch.from_numpy(u0.ravel().copy()).to(dev))
         b.run(max(args.warmup, 3))                  # the first steps run instance by instance
@@ -826,6 +967,26 @@ def run_omega(args):
     print(json.dumps(out), flush=True)
 
 
+def kernel_case(args):
+    """A small run of the workload's kernels for ncu captures: the first time step's predictor solve of
+    the workload's grid in the mixed form (host-driven loops, restart 2, at most 4 Arnoldi steps), so
+    that every pass class, the Arnoldi kernel and the double-float residual passes launch a few times
+    on vectors of the full size."""
+    import torch
+    from paper_2410_03643_gb300 import build, rfnse
+    build.build_library()
+    inst, _ = workload(args.kernel_case, 1)
+    p, u0 = inst[0]
+    p = p.replace(restart=2, max_it=4)
+    s = rfnse.Solver(p, precision=1, device_loop=0)
+    s.set_state(torch.from_numpy(u0.ravel().copy()).to("cuda"))
+    its, _ = s.run(1, allow_noconv=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": args.kernel_case, "n": list(p.n[:p.d]), "arnoldi_steps": int(its[0]),
+                      "launches": rfnse.launch_count()}), flush=True)
+    s.close()
+
+
 def arnoldi_probe():
     """Duration of the cooperative Arnoldi kernel per column j (CUDA events, 20 launches each)."""
     import torch
@@ -855,6 +1016,12 @@ def alu_probe():
 
 def main():
     args = parse()
+    if args.cpu_sample:
+        cpu_sample_child(args)
+        return
+    if args.kernel_case:
+        kernel_case(args)
+        return
     if args.alu_probe:
         alu_probe()
         return

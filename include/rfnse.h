@@ -146,6 +146,12 @@ rfnse_ctx* rfnse_batch_context(rfnse_batch* b, int i);
    ECUDA, ENOCONV (every step is still taken), ENUMERIC, ETIMEOUT. */
 int rfnse_batch_run(rfnse_batch* b, int nsteps, int* iters, double* relres);
 
+/* Autotune every instance (rfnse_autotune, reps timed launches per candidate; each distinct grid is
+   timed once and its choices reused) and drop the batch's captured step graphs so that the next step
+   captures them with the chosen geometries.  n_configs, n_changed (host, may be NULL): summed over the
+   instances.  Errors: EINVAL, ECUDA. */
+int rfnse_batch_autotune(rfnse_batch* b, int reps, int* n_configs, int* n_changed);
+
 /* ---- reverse pass: gradients of a loss of u^N ---------------------------------------------------
  * The paper has no adjoint: these compute the exact derivative of its discrete scheme (eq.
  * 'discretizedCNLSMaxForm' of Sec. 2.1, eq. 'discretizedRFSE2DMaxForm' of Sec. 2.2, and the
@@ -243,6 +249,29 @@ int rfnse_get_coefficients(rfnse_ctx* ctx, double* c, double* lam);
    RFNSE_ECUDA without doing any work.  Errors: EINVAL, ECUDA. */
 int rfnse_apply_prec_static(const rfnse_params* p, const void* v, void* z, const double* D, int half,
                             void* stream);
+
+/* ---- autotuning of the line passes (the paper has no counterpart: a launch-geometry choice) ------ */
+
+/* Choose the launch geometry of every line pass the context's solves run (the DST-I, tau-solve and
+   Toeplitz passes of one axis each): the tile of B lines per block (a power of two; on strided axes B
+   lines adjacent in x), the threads per line of the FFT (runtime-length FFT: one or two radix-4
+   butterflies per thread; fixed-length FP32 FFT: L/8 threads, radix-8 butterflies) and the kernel
+   variant (fixed-length FP32 passes: operands prefetched into registers or staged through shared
+   memory).  Each pass configuration runs once with its real operands (the context's work vectors,
+   which it overwrites; the time-stepping state is untouched), then every candidate geometry is timed
+   with CUDA events over `reps` launches (1..1000) on the context's stream and the fastest is kept in
+   the context; later launches of that configuration use it, and the context's cached solve graphs are
+   dropped so that the next solve captures them again.  Choices are shared between contexts of the same
+   grid on the same device unless force = 1.  The arithmetic of a line does not depend on the
+   geometry; only the order of the first MGS dot product's block partials does, so results agree with
+   an untuned context to rounding.  n_configs, n_changed (host, may be NULL): configurations tuned and
+   how many got a geometry other than the default; est_speedup (host, may be NULL): summed default over
+   summed chosen duration, one launch of each configuration.  Synchronises the stream.
+   Errors: EINVAL, ECUDA. */
+int rfnse_autotune(rfnse_ctx* ctx, int reps, int force, int* n_configs, int* n_changed, double* est_speedup);
+
+/* Number of line-pass launches of ctx whose geometry came from rfnse_autotune's choices. */
+long long rfnse_tuned_launches(const rfnse_ctx* ctx);
 
 /* ---- instrumentation -------------------------------------------------------------------------- */
 

@@ -479,6 +479,13 @@ int rfnse_get_coefficients(rfnse_ctx* c, double* cc, double* lam) {
 
 long long rfnse_launch_count(void) { return g_kernel_launches.load(); }
 
+int rfnse_autotune(rfnse_ctx* c, int reps, int force, int* n_configs, int* n_changed, double* est_speedup) {
+  if (!c || reps < 1 || reps > 1000) return RFNSE_EINVAL;
+  return autotune(c, reps, force, n_configs, n_changed, est_speedup);
+}
+
+long long rfnse_tuned_launches(const rfnse_ctx* c) { return c ? c->tuned_launches : 0; }
+
 int rfnse_test_fail_allocations(long long after) {
   g_alloc_budget.store(after < 0 ? -1 : after);
   return RFNSE_OK;

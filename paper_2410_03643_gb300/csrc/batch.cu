@@ -228,6 +228,31 @@ rfnse_ctx* rfnse_batch_context(rfnse_batch* b, int i) {
   return b->ctx[i];
 }
 
+int rfnse_batch_autotune(rfnse_batch* b, int reps, int* n_configs, int* n_changed) {
+  if (!b || reps < 1 || reps > 1000) return RFNSE_EINVAL;
+  int total = 0, changed = 0;
+  for (int i = 0; i < b->count; ++i) {
+    int nc = 0, ch = 0;
+    const int st = rfnse_autotune(b->ctx[i], reps, 0, &nc, &ch, nullptr);
+    if (st != RFNSE_OK) {
+      b->err = "instance " + std::to_string(i) + ": " + rfnse_last_error(b->ctx[i]);
+      return st;
+    }
+    total += nc;
+    changed += ch;
+  }
+  // the batch graphs hold the old geometries: capture them again on the next step
+  for (int v = 0; v < 3; ++v) {
+    if (b->exec[v]) cudaGraphExecDestroy(b->exec[v]);
+    if (b->graph[v]) cudaGraphDestroy(b->graph[v]);
+    b->exec[v] = nullptr;
+    b->graph[v] = nullptr;
+  }
+  if (n_configs) *n_configs = total;
+  if (n_changed) *n_changed = changed;
+  return RFNSE_OK;
+}
+
 int rfnse_batch_run(rfnse_batch* b, int nsteps, int* iters, double* relres) {
   if (!b || nsteps < 0) return RFNSE_EINVAL;
   int worst = RFNSE_OK;

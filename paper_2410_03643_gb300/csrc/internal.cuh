@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <atomic>
 #include <cstdio>
+#include <functional>
+#include <map>
 #include <string>
 #include <vector>
 #include "../../include/rfnse.h"
@@ -72,6 +74,21 @@ struct SolveCfg {
   int mixed;        // 1: mixed form (inner tolerance from eta_min, FP64 outer residual)
   double tol;       // relative residual tolerance of the solve
   double eta_min;   // mixed form: smallest inner tolerance
+};
+
+// Geometry of a line-pass launch (passes.cuh): lines per block, threads per line, kernel variant
+// (1 = the prefetching fixed-length FP32 kernel, 0 = k_line_pass).
+struct PassGeom {
+  int B, nt, variant;
+};
+
+// One pass configuration seen while rfnse_autotune records a solver's passes: its key, the geometry it
+// gets without tuning, the geometries to try, and a function that launches it with a given geometry.
+struct TuneRecord {
+  unsigned long long key = 0;
+  PassGeom dflt{};
+  std::vector<PassGeom> cands;
+  std::function<cudaError_t(const PassGeom&)> launch;
 };
 
 // Counter and generation of a grid-wide barrier (control.cu); zero-initialised.
@@ -260,6 +277,11 @@ struct rfnse_ctx {
   // per-step statistics of the last solve
   int last_iters = 0, last_outer = 0;
   double last_relres = 0.0;
+  // autotuned pass geometry (rfnse_autotune): per pass configuration the geometry that measured
+  // fastest; empty until tuned.  tune_rec is set only while the tuner records the solver's passes.
+  std::map<unsigned long long, rfnse::PassGeom> tune;
+  std::vector<rfnse::TuneRecord>* tune_rec = nullptr;
+  long long tuned_launches = 0;  // pass launches whose geometry came from `tune`
   // kernel-class profiling (rfnse_profile): CUDA events around every launch of one pass kind
   int prof_kind = 0;
   std::vector<cudaEvent_t> prof_events;  // pairs (start, stop)

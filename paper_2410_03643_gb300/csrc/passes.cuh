@@ -185,6 +185,7 @@ __device__ __forceinline__ void bluestein_lines(cv<R>* buf, int Lp, int L, int l
 }
 
 constexpr int kPassMaxThreads = 512;  // the line-pass kernels' launch bound
+constexpr size_t kPassMaxSmem = 200 * 1024;  // the dynamic shared memory the pass kernels opt in to
 
 template <typename R, typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS, int LOG2L>
 __global__ void __launch_bounds__(kPassMaxThreads) k_line_pass(const PassParams p) {
@@ -760,7 +761,7 @@ struct PassKernels {
       if (lg != 0 && !(sizeof(R) == 4 && fixed_fft_length(lg))) continue;
       for (int pf = 0; pf < 2; ++pf) {
         const cudaError_t r = cudaFuncSetAttribute(get(lg, pf != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   200 * 1024);
+                                                   (int)kPassMaxSmem);
         if (e == cudaSuccess) e = r;
       }
     }
@@ -791,13 +792,55 @@ void pass_work(const PassParams& p, double& flops, double& bytes) {
   }
 }
 
+// Key of a pass configuration for the autotuner: everything that selects the kernel and its geometry
+// (flags, compute precision, operand storage, axis).
 template <typename R, typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS>
-cudaError_t launch_pass(rfnse_ctx* c, PassParams p, cudaStream_t s) {
+unsigned long long pass_key(const rfnse_ctx* c, const PassParams& p) {
+  int axis = 0;
+  for (int a = 0; a < c->d; ++a)
+    if (c->stride[a] == p.stride && c->n[a] == p.n) axis = a;
+  unsigned long long k = (unsigned long long)FLAGS;
+  k |= (unsigned long long)(sizeof(R) == 4) << 8;
+  k |= (unsigned long long)(sizeof(TIN) == 16) << 9;
+  k |= (unsigned long long)(sizeof(TOUT) == 16) << 10;
+  k |= (unsigned long long)(sizeof(TACCI) == 16) << 11;
+  k |= (unsigned long long)(sizeof(TACCO) == 16) << 12;
+  k |= (unsigned long long)axis << 13;
+  return k;
+}
+
+// The geometry a pass gets without tuning: lines per block and threads per line from pass_geometry /
+// pass_geometry_fixed, and on grids of up to about four waves the prefetching kernel (k_line_pass_fixed,
+// ~105 registers, faster there: 2-D 511^2 fused x-pass 18.0 -> 15.2 us), otherwise k_line_pass with its
+// higher occupancy (3-D 255^3: equal or slightly faster).
+template <int FLAGS>
+PassGeom default_pass_geometry(const PassParams& p, bool fixed) {
+  const bool xax = (p.stride == 1);
+  PassGeom g{};
+  if (fixed) pass_geometry_fixed(p.L, xax, xax ? p.nlines : p.stride, p.nlines, g.nt, g.B);
+  else pass_geometry(p.L, xax, xax ? p.nlines : p.stride, g.nt, g.B);
+  const long long grid_est =
+      xax ? (p.nlines + g.B - 1) / g.B : ((p.stride + g.B - 1) / g.B) * (p.nlines / p.stride);
+  g.variant = (fixed && !(FLAGS & F_CIRC) && grid_est <= 4 * 152) ? 1 : 0;
+  return g;
+}
+
+// Launch one pass with an explicit geometry g (lines per block B, threads per line nt, kernel variant:
+// 1 = the prefetching fixed-length kernel).  A geometry the kernels cannot run (threads beyond the
+// launch bound, a thread count the FFT does not support, shared memory beyond the opt-in limit) is
+// refused before any launch: inside a stream capture a failed launch would invalidate the capture.
+template <typename R, typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS>
+cudaError_t launch_pass_geom(rfnse_ctx* c, PassParams p, cudaStream_t s, const PassGeom& g) {
   using V = cv<R>;
   const bool xax = (p.stride == 1);
   const bool fixed = sizeof(R) == 4 && fixed_fft_length(p.log2L);
-  if (fixed) pass_geometry_fixed(p.L, xax, xax ? p.nlines : p.stride, p.nlines, p.nt, p.B);
-  else pass_geometry(p.L, xax, xax ? p.nlines : p.stride, p.nt, p.B);
+  p.B = g.B;
+  p.nt = g.nt;
+  const bool prefetch = fixed && !(FLAGS & F_CIRC) && g.variant == 1;
+  if (p.B < 1 || (p.B & (p.B - 1)) != 0 || p.B * p.nt > kPassMaxThreads || p.B * p.nt < 1)
+    return cudaErrorInvalidConfiguration;
+  if (fixed ? (p.nt != (p.L >> kFixedLogR)) : (p.nt != p.L / 4 && p.nt != p.L / 8))
+    return cudaErrorInvalidConfiguration;
   p.dst_scale_f = (float)p.dst_scale;
   p.ca_f = make_float2((float)p.ca.x, (float)p.ca.y);
   p.cb_f = make_float2((float)p.cb.x, (float)p.cb.y);
@@ -812,16 +855,11 @@ cudaError_t launch_pass(rfnse_ctx* c, PassParams p, cudaStream_t s) {
     const long long nhi = p.nlines / p.stride;
     grid = p.tiles_inner * nhi;
   }
-  // tile; twiddles staged in shared memory (all but the fixed-length Bluestein passes, which read
+  // tile; twiddles staged in shared memory (all but the fixed-length passes of k_line_pass, which read
   // them through L1); z of the x-Toeplitz pass saved in shared memory (k_line_pass only)
-  // grids of up to about four waves wait on latency: the prefetching kernel (k_line_pass_fixed, ~105
-  // registers) is faster there; larger grids keep k_line_pass and its higher occupancy (2-D 511^2:
-  // fused x-pass 18.0 -> 15.2 us; 3-D 255^3: equal or slightly slower with the prefetching kernel)
-  const long long grid_est = xax ? (p.nlines + p.B - 1) / p.B : ((p.stride + p.B - 1) / p.B) * (p.nlines / p.stride);
-  const bool prefetch = grid_est <= 4 * 152;
-  const bool regz = fixed && !(FLAGS & F_CIRC) && prefetch;
-  size_t smem = ((size_t)p.B * fft_line_stride(p.L) + ((fixed && !regz) ? 0 : p.L)) * sizeof(V);
-  if ((FLAGS & F_TOEP_X) && !regz) smem += (size_t)p.B * p.n * sizeof(V);
+  size_t smem = ((size_t)p.B * fft_line_stride(p.L) + ((fixed && !prefetch) ? 0 : p.L)) * sizeof(V);
+  if ((FLAGS & F_TOEP_X) && !prefetch) smem += (size_t)p.B * p.n * sizeof(V);
+  if (smem > kPassMaxSmem) return cudaErrorInvalidConfiguration;
   using K = PassKernels<R, TIN, TOUT, TACCI, TACCO, FLAGS>;
   const auto kern = K::get(fixed ? p.log2L : 0, prefetch);
   static const cudaError_t attr_err = K::allow_smem();
@@ -829,14 +867,11 @@ cudaError_t launch_pass(rfnse_ctx* c, PassParams p, cudaStream_t s) {
   if constexpr ((FLAGS & F_DOT0) != 0) {  // too many partials for the Arnoldi kernel to sum: plain pass
     if (grid > kDot0MaxBlocks || grid <= 0) {
       c->dot0_blocks = 0;
-      return launch_pass<R, TIN, TOUT, TACCI, TACCO, FLAGS & ~F_DOT0>(c, p, s);
+      return launch_pass_geom<R, TIN, TOUT, TACCI, TACCO, FLAGS & ~F_DOT0>(c, p, s, g);
     }
     c->dot0_blocks = (int)grid;
   }
   if (grid <= 0) return cudaSuccess;
-  // a block above the launch bound would fail to launch (inside a stream capture that invalidates the
-  // whole capture): refuse it here, before any launch
-  if (p.B * p.nt > kPassMaxThreads || p.B * p.nt < 1) return cudaErrorInvalidConfiguration;
   const int kind = FLAGS | (sizeof(R) == 4 ? 256 : 0);
   const bool prof = c->prof_kind != 0 && ((c->prof_kind | F_INSCALE | F_DOT0) == (kind | F_INSCALE | F_DOT0));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -862,6 +897,62 @@ cudaError_t launch_pass(rfnse_ctx* c, PassParams p, cudaStream_t s) {
     c->prof_bytes += by;
   }
   return cudaGetLastError();
+}
+
+// The geometries the autotuner tries for a pass: every power-of-two tile that fits the launch bound,
+// the lines available and the shared memory; both FFT thread schedules of the runtime-length FFT (one
+// or two radix-4 butterflies per thread); both kernels of the fixed-length FP32 FFT.
+template <int FLAGS>
+std::vector<PassGeom> pass_candidates(const PassParams& p, bool fixed, size_t elem) {
+  std::vector<PassGeom> out;
+  const bool xax = (p.stride == 1);
+  const long long avail = xax ? p.nlines : p.stride;
+  std::vector<int> nts;
+  if (fixed) nts.push_back(p.L >> kFixedLogR);
+  else {
+    if (p.L / 4 <= kPassMaxThreads) nts.push_back(p.L / 4);
+    if (p.L / 8 >= 1) nts.push_back(p.L / 8);
+  }
+  for (int nt : nts)
+    for (int B = 1; B * nt <= kPassMaxThreads && B <= 64; B <<= 1) {
+      if (B > 1 && B > avail) break;
+      for (int variant = 0; variant < ((fixed && !(FLAGS & F_CIRC)) ? 2 : 1); ++variant) {
+        const bool pf = variant == 1;
+        size_t smem = ((size_t)B * fft_line_stride(p.L) + ((fixed && !pf) ? 0 : p.L)) * elem;
+        if ((FLAGS & F_TOEP_X) && !pf) smem += (size_t)B * p.n * elem;
+        if (smem > kPassMaxSmem) continue;
+        out.push_back(PassGeom{B, nt, variant});
+      }
+    }
+  return out;
+}
+
+template <typename R, typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS>
+cudaError_t launch_pass(rfnse_ctx* c, PassParams p, cudaStream_t s) {
+  const bool fixed = sizeof(R) == 4 && fixed_fft_length(p.log2L);
+  PassGeom g = default_pass_geometry<FLAGS>(p, fixed);
+  if (c->tune_rec || !c->tune.empty()) {
+    const unsigned long long key = pass_key<R, TIN, TOUT, TACCI, TACCO, FLAGS>(c, p);
+    if (c->tune_rec) {  // rfnse_autotune is recording the solver's pass configurations
+      bool seen = false;
+      for (const TuneRecord& r : *c->tune_rec) seen = seen || r.key == key;
+      if (!seen) {
+        TuneRecord r;
+        r.key = key;
+        r.dflt = g;
+        r.cands = pass_candidates<FLAGS>(p, fixed, sizeof(cv<R>));
+        r.launch = [c, p, s](const PassGeom& gg) { return launch_pass_geom<R, TIN, TOUT, TACCI, TACCO, FLAGS>(c, p, s, gg); };
+        c->tune_rec->push_back(std::move(r));
+      }
+    } else {
+      const auto it = c->tune.find(key);
+      if (it != c->tune.end()) {
+        g = it->second;
+        c->tuned_launches += 1;
+      }
+    }
+  }
+  return launch_pass_geom<R, TIN, TOUT, TACCI, TACCO, FLAGS>(c, p, s, g);
 }
 
 }  // namespace rfnse

@@ -9,6 +9,9 @@
 // Both run the same algorithm on the same kernels' arithmetic.
 #include <algorithm>
 #include <cmath>
+#include <limits>
+#include <mutex>
+#include <tuple>
 #include "internal.cuh"
 #include "passes.cuh"
 #include "solve.cuh"
@@ -620,6 +623,161 @@ rfnse_status time_step(rfnse_ctx* c, int* iters, double* relres) {
   c->step += 1;
   *iters = it;
   return st;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Autotuner of the line passes (rfnse_autotune).  The tuner runs the passes of one Arnoldi step and of
+// the solver's other products once in recording mode, so that every pass configuration the solves
+// launch is seen with its real operands; then it times each configuration under every candidate
+// geometry (tile of B lines, threads per line, kernel variant) with CUDA events and keeps the fastest
+// in the context.  Choices are shared between contexts of the same grid on the same device (a batch of
+// many instances tunes each distinct grid once).
+
+namespace {
+
+using TuneMemoKey = std::tuple<int, int, int, int, int, unsigned long long>;  // device, d, n0, n1, n2, key
+std::mutex g_tune_mutex;
+std::map<TuneMemoKey, std::pair<PassGeom, PassGeom>> g_tune_memo;  // (best, default)
+std::map<TuneMemoKey, std::pair<double, double>> g_tune_times;     // (best us, default us)
+
+// Mean duration in microseconds of `reps` launches of one configuration with geometry g (one untimed
+// launch first); +inf if the geometry cannot launch.
+double time_geometry(rfnse_ctx* c, const TuneRecord& r, const PassGeom& g, int reps, cudaEvent_t e0,
+                     cudaEvent_t e1) {
+  if (r.launch(g) != cudaSuccess) {
+    cudaGetLastError();
+    return std::numeric_limits<double>::infinity();
+  }
+  cudaEventRecord(e0, c->stream);
+  for (int i = 0; i < reps; ++i)
+    if (r.launch(g) != cudaSuccess) {
+      cudaGetLastError();
+      cudaStreamSynchronize(c->stream);
+      return std::numeric_limits<double>::infinity();
+    }
+  cudaEventRecord(e1, c->stream);
+  if (cudaEventSynchronize(e1) != cudaSuccess) return std::numeric_limits<double>::infinity();
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  return 1e3 * ms / reps;
+}
+
+// Run, in recording mode, every line-pass configuration the context's solves launch: the Arnoldi
+// step's preconditioner and product (with the first MGS dot product), the solution update, and the
+// FP64 products of the right-hand side and the residual.  The operands are the context's own work
+// vectors (zeroed; their contents do not change a pass's duration).
+cudaError_t record_solver_passes(rfnse_ctx* c, std::vector<TuneRecord>* rec) {
+  const long long N = c->N;
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  chk(cudaMemsetAsync(c->D, 0, sizeof(double) * N, s));
+  chk(cudaMemsetAsync(c->r, 0, sizeof(double2) * N, s));
+  chk(cudaMemsetAsync(c->x, 0, sizeof(double2) * N, s));
+  chk(cudaMemsetAsync(c->f, 0, sizeof(double2) * N, s));
+  chk(cudaMemsetAsync(c->w, 0, sizeof(double2) * N, s));
+  chk(prepare_D(c, c->D));
+  if (e != cudaSuccess) return e;
+  Dyn dot0;
+  dot0.vbase = c->V;
+  dot0.dot0 = true;
+  c->tune_rec = rec;
+  for (int half = 0; half < 2 && e == cudaSuccess; ++half) {
+    if (c->p.precision == 1) {
+      chk((run_precon<float, double2, float2, float2, float2, true, true>(
+          c, c->r, &c->gs->inv_beta, c->V, c->Z32, 0, c->D, c->w, c->wp32, nullptr, kOne, kI, half, c->t1f, c->t2f,
+          dot0)));
+    } else {
+      chk((run_precon<double, double2, double2, double2, double2, true, true>(
+          c, c->r, &c->gs->inv_beta, c->V, c->zb, 0, c->D, c->w, c->w, nullptr, kOne, kI, half, c->t1, c->t2,
+          dot0)));
+      chk((run_precon<double, double2, double2, double2, double2, false, false>(
+          c, c->r, nullptr, nullptr, c->x, 1, c->D, nullptr, nullptr, nullptr, kOne, kI, half, c->t1, c->t2)));
+    }
+    chk(run_matvec_fp64(c, c->x, c->D, c->r, c->f, kMinusOne, kMinusI, half, nullptr));
+  }
+  c->tune_rec = nullptr;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+}
+
+}  // namespace
+
+rfnse_status autotune(rfnse_ctx* c, int reps, int force, int* n_configs, int* n_changed, double* est_speedup) {
+  int dev = 0;
+  RFNSE_CUDA_TRY(c, cudaGetDevice(&dev));
+  std::vector<TuneRecord> rec;
+  c->tune.clear();
+  RFNSE_CUDA_TRY(c, record_solver_passes(c, &rec));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  RFNSE_CUDA_TRY(c, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    c->err = "autotune: event creation failed";
+    return RFNSE_ECUDA;
+  }
+  int changed = 0;
+  double t_best = 0.0, t_dflt = 0.0;
+  rfnse_status st = RFNSE_OK;
+  for (const TuneRecord& r : rec) {
+    const TuneMemoKey mk{dev, c->d, c->n[0], c->n[1], c->n[2], r.key};
+    PassGeom best = r.dflt;
+    double tb = 0.0, td = 0.0;
+    bool have = false;
+    if (!force) {
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      const auto it = g_tune_memo.find(mk);
+      if (it != g_tune_memo.end()) {
+        best = it->second.first;
+        tb = g_tune_times[mk].first;
+        td = g_tune_times[mk].second;
+        have = true;
+      }
+    }
+    if (!have) {
+      td = time_geometry(c, r, r.dflt, reps, e0, e1);
+      tb = td;
+      for (const PassGeom& g : r.cands) {
+        const double t = time_geometry(c, r, g, reps, e0, e1);
+        if (t < tb) {
+          tb = t;
+          best = g;
+        }
+      }
+      if (!(td < std::numeric_limits<double>::infinity())) {
+        st = RFNSE_ECUDA;
+        c->err = "autotune: a pass failed with its default geometry";
+        break;
+      }
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      g_tune_memo[mk] = {best, r.dflt};
+      g_tune_times[mk] = {tb, td};
+    }
+    c->tune[r.key] = best;
+    if (best.B != r.dflt.B || best.nt != r.dflt.nt || best.variant != r.dflt.variant) ++changed;
+    t_best += tb;
+    t_dflt += td;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != RFNSE_OK) {
+    c->tune.clear();
+    return st;
+  }
+  // the cached solve graphs hold the old geometries: capture them again on the next solve
+  for (int a = 0; a < 2; ++a)
+    for (int h = 0; h < 2; ++h) {
+      if (c->graph_exec[a][h]) cudaGraphExecDestroy(c->graph_exec[a][h]);
+      if (c->graph[a][h]) cudaGraphDestroy(c->graph[a][h]);
+      c->graph_exec[a][h] = nullptr;
+      c->graph[a][h] = nullptr;
+    }
+  if (n_configs) *n_configs = (int)rec.size();
+  if (n_changed) *n_changed = changed;
+  if (est_speedup) *est_speedup = (t_best > 0.0) ? t_dflt / t_best : 1.0;
+  return RFNSE_OK;
 }
 
 }  // namespace rfnse

@@ -19,6 +19,9 @@ rfnse_status tban_solve(rfnse_ctx* c, const double* D, const double2* f, double2
                         double* relres);
 cudaError_t prepare_D(rfnse_ctx* c, const double* D);
 // f_part / f_n: block partials of ||f||^2 left by f's producer in the same graph (f_n = 0: none)
+// rfnse_autotune: tune the geometry of every line-pass configuration of c's solves (reps timed launches
+// per candidate; force = 1 ignores choices made for the same grid by other contexts)
+rfnse_status autotune(rfnse_ctx* c, int reps, int force, int* n_configs, int* n_changed, double* est_speedup);
 cudaError_t capture_solve(rfnse_ctx* c, int mixed, int half, cudaGraph_t g, cudaStream_t s,
                           const double* f_part = nullptr, int f_n = 0);
 

@@ -57,7 +57,8 @@ EXPORTED = ("rfnse_default_params", "rfnse_create", "rfnse_destroy", "rfnse_last
             "rfnse_profile", "rfnse_profile_read", "rfnse_probe_fma", "rfnse_probe_arnoldi", "rfnse_batch_create",
             "rfnse_batch_destroy", "rfnse_batch_last_error", "rfnse_batch_context", "rfnse_batch_run",
             "rfnse_tape_forward", "rfnse_tape_backward", "rfnse_adjoint_solve", "rfnse_tban_solve",
-            "rfnse_selftest_bounded_wait", "rfnse_test_fail_allocations", "rfnse_apply_prec_static")
+            "rfnse_selftest_bounded_wait", "rfnse_test_fail_allocations", "rfnse_apply_prec_static",
+            "rfnse_autotune", "rfnse_tuned_launches", "rfnse_batch_autotune")
 
 K_INSCALE, K_DST, K_LAM, K_DSCALE, K_TOEP_X, K_TOEP_ACC, K_FP32, K_DF, K_ARNOLDI = 1, 2, 4, 8, 16, 32, 256, 1024, 2048
 
@@ -132,6 +133,12 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.rfnse_tban_solve.restype = ip
     lib.rfnse_selftest_bounded_wait.argtypes = [vp, ctypes.POINTER(ctypes.c_int), dp]
     lib.rfnse_selftest_bounded_wait.restype = ip
+    lib.rfnse_autotune.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), dp]
+    lib.rfnse_autotune.restype = ip
+    lib.rfnse_tuned_launches.argtypes = [vp]
+    lib.rfnse_tuned_launches.restype = ctypes.c_longlong
+    lib.rfnse_batch_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.rfnse_batch_autotune.restype = ip
     lib.rfnse_test_fail_allocations.argtypes = [ctypes.c_longlong]
     lib.rfnse_test_fail_allocations.restype = ip
     if path == _build.library_path():
@@ -367,6 +374,17 @@ class Solver:
         self._check(self.lib.rfnse_tape_backward(self.h, _ptr(gN), _ptr(g0), ctypes.byref(grho), ctypes.byref(it), 1))
         return g0, grho.value, it.value
 
+    def autotune(self, reps: int = 5, force: bool = False):
+        """Tune the launch geometry of the solver's line passes (rfnse_autotune); returns (configurations
+        tuned, configurations whose geometry changed, estimated speed-up of one launch of each)."""
+        nc, ch, sp = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._check(self.lib.rfnse_autotune(self.h, int(reps), int(force), ctypes.byref(nc), ctypes.byref(ch),
+                                            ctypes.byref(sp)))
+        return nc.value, ch.value, sp.value
+
+    def tuned_launches(self) -> int:
+        return int(self.lib.rfnse_tuned_launches(self.h))
+
     def profile(self, kind: int):
         """Time every launch of kernel class `kind` (K_* flags; 0 = off)."""
         self._check(self.lib.rfnse_profile(self.h, kind))
@@ -439,6 +457,16 @@ class Batch:
         step = ctypes.c_int()
         self._check(self.lib.rfnse_get_state(self.ctx[i], _ptr(up), _ptr(uc), ctypes.byref(step), 1), self.ctx[i])
         return up, uc, step.value
+
+    def autotune(self, reps: int = 5):
+        """Tune every instance's line passes (each distinct grid once); returns (configurations tuned,
+        configurations whose geometry changed), summed over the instances."""
+        nc, ch = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.rfnse_batch_autotune(self.h, int(reps), ctypes.byref(nc), ctypes.byref(ch)))
+        return nc.value, ch.value
+
+    def tuned_launches(self) -> int:
+        return sum(int(self.lib.rfnse_tuned_launches(c)) for c in self.ctx)
 
     def run(self, nsteps: int, allow_noconv: bool = False):
         """Advance every instance nsteps; returns (iters, relres) of shape (nsteps, count)."""

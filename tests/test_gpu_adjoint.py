@@ -133,12 +133,16 @@ def test_gradient_workload_full_size(first_step):
     s.close()
 
 
-def test_autograd_rollout_finite_differences():
-    """torch.autograd through rollout(): 8 seeded directions in u0 and the rho direction, central
-    differences with h = 1e-6 of the GPU forward."""
+@pytest.mark.parametrize("n", (127, 255))
+def test_autograd_rollout_finite_differences(n):
+    """torch.autograd through rollout() on the gradient workload (255^2, alpha = 1.5, rho = 2, dt = 0.005,
+    20 steps, FP64; and the same at 127^2): 8 seeded directions in u0 and the rho direction, central
+    differences with h = 1e-6 of the GPU forward, agreement to 1e-6 relative.  The solves run at tol
+    1e-13 so that the forward map's own error (a jump of about tol in u^N wherever an iteration count
+    changes) stays far below what h = 1e-6 resolves."""
     from paper_2410_03643_gb300 import rollout
-    p, u0, nsteps, u0t, rho_t = W.config_adjoint(n=127)
-    p = p.replace(tol=1e-12)
+    p, u0, nsteps, u0t, rho_t = W.config_adjoint(n=n)
+    p = p.replace(tol=1e-13)
     target = rollout(p, dev(u0t), torch.tensor(rho_t, dtype=torch.float64), nsteps).detach()
     x = dev(u0).requires_grad_(True)
     rho = torch.tensor(p.rho, dtype=torch.float64, requires_grad=True)
@@ -154,10 +158,13 @@ def test_autograd_rollout_finite_differences():
     h = 1e-6
     dirs, _ = W.fd_directions(p.shape, 8)
     scale = np.linalg.norm(u0)
+    errs = []
     for d in dirs:
         d = d * scale
         fd = (L(u0 + h * d, p.rho) - L(u0 - h * d, p.rho)) / (2 * h)
         ad = float(np.real(np.vdot(g0, d.ravel())))
-        assert abs(fd - ad) <= 1e-5 * abs(fd) + 1e-9, (fd, ad)
+        errs.append(abs(fd - ad) / abs(fd))
     fd = (L(u0, p.rho + h) - L(u0, p.rho - h)) / (2 * h)
-    assert abs(fd - float(rho.grad)) <= 1e-5 * abs(fd) + 1e-9, (fd, float(rho.grad))
+    errs.append(abs(fd - float(rho.grad)) / abs(fd))
+    print(f"adjoint vs central differences, n = {n}: relative errors {[f'{e:.2e}' for e in errs]}")
+    assert max(errs) < 1e-6, errs

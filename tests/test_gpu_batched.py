@@ -86,24 +86,39 @@ def test_batch_state_reload_and_continue():
     b.close()
 
 
-def test_batched_workload_64_uneven_instances_sampled():
-    """The 64-instance workload (n_x, n_y from {127, 255, 511}, seed 2410), mixed form, 4 steps; the
-    smallest, a middle and the largest instance checked against the oracle, every instance finite."""
+@pytest.mark.parametrize("precision", (1, 0))
+def test_batched_workload_64_uneven_instances_every_instance(precision):
+    """The 64-instance workload (n_x, n_y from {127, 255, 511}, seed 2410), 4 steps through the batch
+    (from the second step on one graph launch per step for all instances): every instance's u^4 against
+    the oracle, 1e-10 (FP64 form) / 1e-8 (mixed form) relative L2, iteration counts within +-1 (FP64)."""
     from paper_2410_03643_gb300 import Batch
     inst, _ = W.config_batched()
     nsteps = 4
-    b = Batch([p for p, _ in inst], precision=1)
+    b = Batch([p for p, _ in inst], precision=precision)
     for i, (p, u0) in enumerate(inst):
         b.set_state(i, dev(u0))
     iters, _ = b.run(nsteps)
     assert np.all(iters >= 1)
-    order = sorted(range(len(inst)), key=lambda i: inst[i][0].size)
-    for i in (order[0], order[len(order) // 2], order[-1]):
-        p, u0 = inst[i]
-        _, uc, _ = b.get_state(i)
-        ref, _, _ = SchemeOracle(p).run(u0, nsteps)
-        assert rel(uc.cpu().numpy().reshape(p.shape), ref[-1]) < 1e-8, i
-    for i in range(len(inst)):
+    tol = 1e-10 if precision == 0 else 1e-8
+    worst = 0.0
+    for i, (p, u0) in enumerate(inst):
         _, uc, step = b.get_state(i)
-        assert step == nsteps and np.isfinite(float(torch.linalg.vector_norm(uc)))
+        assert step == nsteps
+        ref, its_ref, _ = _oracle_batched(i, nsteps)
+        err = rel(uc.cpu().numpy().reshape(p.shape), ref[-1])
+        worst = max(worst, err)
+        assert err < tol, (i, err)
+        if precision == 0:
+            assert all(abs(int(a) - int(r)) <= 1 for a, r in zip(iters[:, i], its_ref)), (i, iters[:, i], its_ref)
     b.close()
+
+
+_ORACLE_BATCHED = {}
+
+
+def _oracle_batched(i, nsteps):
+    if (i, nsteps) not in _ORACLE_BATCHED:
+        inst, _ = W.config_batched()
+        p, u0 = inst[i]
+        _ORACLE_BATCHED[(i, nsteps)] = SchemeOracle(p).run(u0, nsteps)
+    return _ORACLE_BATCHED[(i, nsteps)]

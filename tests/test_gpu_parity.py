@@ -267,12 +267,40 @@ def test_config_1d_full_trajectory_fp64():
         assert abs(int(iters[k]) - its_ref[k]) <= 1
 
 
+@pytest.fixture(scope="module")
+def oracle_3d_255():
+    """The oracle's first two steps of the 3-D workload (n = 255^3, alpha = 1.7, rho = 1, dt = 0.01) at
+    tolerance 1e-10: at the workload's own 1e-8 two solutions that both meet the tolerance may differ by
+    about 2e-8, which would hide a 1e-10 disagreement."""
+    p, u0, _ = W.config_3d()
+    p = p.replace(tol=1e-10)
+    traj, its, _ = SchemeOracle(p).run(u0, 2)
+    return p, u0, traj, its
+
+
+@pytest.mark.parametrize("precision", (0, 1))
+def test_config_3d_255_first_two_steps_match_the_oracle(oracle_3d_255, precision):
+    """The full-size 3-D workload, element by element: u^1 (the first step, predictor and corrector)
+    and u^2 (the first regular step) against the oracle to 1e-10 (FP64 form) and 1e-8 (mixed form)
+    relative L2, with the iteration counts within +-1 (FP64 form)."""
+    p, u0, ref, its_ref = oracle_3d_255
+    s = Solver(p, precision=precision)
+    s.set_state(dev(u0))
+    traj = torch.empty(2 * p.size, dtype=torch.complex128, device="cuda")
+    iters, _ = s.run(2, traj)
+    s.close()
+    got = traj.cpu().numpy().reshape((2,) + p.shape)
+    del traj
+    for k in range(2):
+        assert rel(got[k], ref[k]) < (1e-10 if precision == 0 else 1e-8), (k, rel(got[k], ref[k]))
+        if precision == 0:
+            assert abs(int(iters[k]) - its_ref[k]) <= 1, (k, iters, its_ref)
+
+
 @pytest.mark.parametrize("precision", (1, 0))
 def test_config_3d_255_steps_solve_the_printed_system(precision):
-    """d=3, n=255^3, alpha=1.7, rho=1, dt=0.01, tol 1e-8 (full size; the oracle cannot run whole
-    trajectories here in test time).  Property check with the oracle's own operators: the GPU's u^2
-    solves (D - T + iI) u^2 = (T - D + iI) u^0 with D = rho dt |u^1|^2 to the tolerance, and
-    ||u^2|| = ||u^0|| (the scheme is a Cayley transform)."""
+    """The 3-D workload at its own tolerance 1e-8: the GPU's u^2 solves (D - T + iI) u^2 = (T - D + iI) u^0
+    with D = rho dt |u^1|^2 to the tolerance, and ||u^2|| = ||u^0|| (the scheme is a Cayley transform)."""
     p, u0, _ = W.config_3d()
     s = Solver(p, precision=precision)
     s.set_state(dev(u0))
@@ -291,13 +319,31 @@ def test_config_3d_255_steps_solve_the_printed_system(precision):
     assert 1 <= iters[1] <= 20
 
 
+_ORACLE_2D = {}
+
+
+def _oracle_2d(alpha, nsteps):
+    if alpha not in _ORACLE_2D:
+        p, u0, _ = W.config_2d(alpha)
+        _ORACLE_2D[alpha] = SchemeOracle(p).run(u0, nsteps)
+    return _ORACLE_2D[alpha]
+
+
 @pytest.mark.parametrize("alpha", W.CONFIG_2D_ALPHAS)
 @pytest.mark.parametrize("precision", (0, 1))
-def test_config_2d_511_first_steps(alpha, precision):
-    """d=2, n=511^2, dt=0.005: the first three steps of the full-size workload against the oracle."""
+def test_config_2d_511_first_ten_steps(alpha, precision):
+    """d=2, n=511^2, dt=0.005: the first ten steps of the full-size workload against the oracle, every
+    step element by element."""
+    nsteps = 10
     p, u0, _ = W.config_2d(alpha)
-    got, iters, ref, its_ref = _traj_case(p, 3, precision, u0)
-    for k in range(3):
+    s = Solver(p, precision=precision)
+    s.set_state(dev(u0))
+    traj = torch.empty(nsteps * p.size, dtype=torch.complex128, device="cuda")
+    iters, _ = s.run(nsteps, traj)
+    s.close()
+    got = traj.cpu().numpy().reshape((nsteps,) + p.shape)
+    ref, its_ref, _ = _oracle_2d(alpha, nsteps)
+    for k in range(nsteps):
         assert rel(got[k], ref[k]) < (1e-10 if precision == 0 else 1e-8), (k, rel(got[k], ref[k]))
         if precision == 0:
             assert abs(int(iters[k]) - its_ref[k]) <= 1
