@@ -145,6 +145,8 @@ def parse():
                     help="only time the cooperative Arnoldi kernel (MGS + Givens) per column j on the 2-D and "
                          "3-D grid sizes and print the times")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch geometry of the line passes")
+    ap.add_argument("--no-lockstep", action="store_true",
+                    help="batches run one CUDA graph branch per instance instead of the lock-step launches")
     ap.add_argument("--no-3d", action="store_true",
                     help="default 2d workload: leave out the 3-D 255^3 half of the metric (config_3d)")
     ap.add_argument("--kernel-case", default=None, choices=["2d", "3d"],
@@ -472,6 +474,8 @@ def measure(args, env: Env, name: str, instances: int, steps: int, warmup: int, 
             device_loop = 0 if args.host_loop else 1
         if use_batch if batch is None else batch:
             b = rfnse.Batch([p for p, _ in inst], precision=precision, stream=main, device_loop=device_loop)
+            if args.no_lockstep and b.lockstep:
+                b.set_lockstep(False)
             if not args.no_autotune:
                 nc, ch = b.autotune(reps=5)
                 tuning.setdefault(precision, {"configs": nc, "changed": ch})
@@ -558,6 +562,9 @@ def measure(args, env: Env, name: str, instances: int, steps: int, warmup: int, 
 
     # headline: mixed form
     mixed = make(1)
+    lockstep_note = ("lock-step: every launch of a step covers all instances (work-list line passes, one "
+                     "cooperative Gram-Schmidt launch)" if isinstance(mixed, rfnse.Batch) and mixed.lockstep
+                     else None)
     clocks = ClockSampler(env.local) if rank == 0 else None
     if clocks:
         clocks.start()
@@ -578,7 +585,8 @@ def measure(args, env: Env, name: str, instances: int, steps: int, warmup: int, 
                                           "one CUDA stream and host thread per instance" if concurrent
                                           else "instances in turn on one stream")),
                           control=("host-driven GMRES loops" if args.host_loop
-                                   else "device-decided GMRES loops, one CUDA graph per solve")),
+                                   else "device-decided GMRES loops, one CUDA graph per solve"),
+                          lockstep=lockstep_note),
            "gpu_launches": launches,
            "iters_per_solve_mean": float(np.mean(iters_m)) if iters_m else None}
     if clk:
@@ -747,6 +755,8 @@ def run_batched(args):
 
     def timed(precision, clocks=None):
         b = rfnse.Batch([p for p, _ in inst], precision=precision, stream=main)
+        if args.no_lockstep and b.lockstep:
+            b.set_lockstep(False)
         if not args.no_autotune:
             b.autotune(reps=5)                      # every distinct grid timed once (set-up, not timed)
         for i, (p, u0) in enumerate(inst):
@@ -771,8 +781,11 @@ def run_batched(args):
         ms = sum(a.elapsed_time(e) for a, e in evs)
         launches = rfnse.launch_count() - l0
         states = [b.get_state(i)[1] for i in range(b.count)]
+        modes.append(b.lockstep)
         b.close()
         return ms, launches, np.array(its), states
+
+    modes = []
 
     clocks = ClockSampler(local) if rank == 0 else None
     if clocks:
@@ -785,7 +798,8 @@ def run_batched(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
            "data": "synthetic (closed-form initial data of the paper's shape, seeded parameters)",
            "config": dict(desc, precision="mixed", l2="256 MiB buffer written between timed steps",
-                          parallelism=f"{world} GPU(s); one CUDA graph launch per batch step"),
+                          parallelism=f"{world} GPU(s); one CUDA graph launch per batch step",
+                          lockstep=bool(modes and modes[0])),
            "gpu_launches": launches, "iters_per_solve_mean": float(its.mean())}
     if clk:
         out["clocks"] = clk
@@ -979,6 +993,8 @@ def kernel_case(args):
     p, u0 = inst[0]
     p = p.replace(restart=2, max_it=4)
     s = rfnse.Solver(p, precision=1, device_loop=0)
+    if not args.no_autotune:
+        s.autotune(reps=5)                 # the geometry the bench's solvers launch with
     s.set_state(torch.from_numpy(u0.ravel().copy()).to("cuda"))
     its, _ = s.run(1, allow_noconv=True)
     torch.cuda.synchronize()

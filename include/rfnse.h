@@ -24,6 +24,13 @@
  *   stream).  Entry points that return statistics to the host synchronise that stream.
  * Errors: every call returns an rfnse_status; no C++ exception crosses the ABI.  After an error,
  *   rfnse_last_error(ctx) describes it.  RFNSE_ENOCONV still writes the best iterate.
+ * Debug mode: with the environment variable RFNSE_DEBUG=1 when rfnse_create runs, the context drives
+ *   its loops from the host (as device_loop = 0) and checks every line pass after its launch: that its
+ *   tiles cover the grid exactly, that it launched and ran without a CUDA error, and whether its
+ *   outputs hold non-finite values.  The first pass that wrote one is named by rfnse_last_error when
+ *   rfnse_run then returns RFNSE_ENUMERIC.  Every pass synchronises the stream, so this is slow.
+ *   Profilers can group kernels by the NVTX ranges "rfnse step", "rfnse solve", "rfnse pass",
+ *   "rfnse pass group", "rfnse autotune", "rfnse tape forward" and "rfnse reverse pass".
  */
 #ifndef RFNSE_H
 #define RFNSE_H
@@ -145,6 +152,27 @@ rfnse_ctx* rfnse_batch_context(rfnse_batch* b, int i);
    failure, rfnse_batch_last_error naming its instance, without taking further steps.  Errors: EINVAL,
    ECUDA, ENOCONV (every step is still taken), ENUMERIC, ETIMEOUT. */
 int rfnse_batch_run(rfnse_batch* b, int nsteps, int* iters, double* relres);
+
+/* Lock-step mode of a batch (the paper has no counterpart: a scheduling choice).  The instances'
+   solves advance together: one time step is one CUDA graph launch in which every Arnoldi step of all
+   instances still iterating is one launch per line pass over a work list of every instance's
+   (instance, tile) items, grouped by FFT length, plus one cooperative launch of modified Gram-Schmidt
+   and Givens over all instances' vectors (blocks shared in proportion to their sizes, the grid-wide
+   barrier after each sweep common to all); each refinement cycle's bookkeeping (back-substitution,
+   solution update, residual product or recurrence, norm and refinement decision) is one launch for all
+   instances.  Each instance keeps its own basis, Hessenberg matrix, rotations, tolerance and
+   convergence; an instance that has finished its cycle or its solve skips its share of a launch, and
+   the graph's loops run while any instance iterates.  Results equal those of the per-instance graphs
+   up to the order of partial sums.  Available for batches of mixed-precision (precision 1) instances of
+   one dimension with the sine-transform preconditioner (precond 0) and n[a] + 1 in 128..1024 on every
+   axis, at most 1024 instances.  Such batches of at least 8 instances start in this mode (measured: 64
+   uneven 2-D instances run faster lock-step, three 511^2 instances faster as concurrent per-instance
+   graphs).  on = 0 switches to one CUDA graph branch per instance, on = 1 to lock-step.
+   Errors: EINVAL (on = 1 for a batch that does not qualify). */
+int rfnse_batch_set_lockstep(rfnse_batch* b, int on);
+
+/* 1 when batch b runs its steady steps in lock-step mode, else 0. */
+int rfnse_batch_lockstep(const rfnse_batch* b);
 
 /* Autotune every instance (rfnse_autotune, reps timed launches per candidate; each distinct grid is
    timed once and its choices reused) and drop the batch's captured step graphs so that the next step

@@ -155,6 +155,7 @@ using namespace rfnse;
 extern "C" {
 
 int rfnse_tape_forward(rfnse_ctx* c, const void* u0, int nsteps, int every, void* uN, int* iters, int on_device) {
+  NvtxRange range("rfnse tape forward");
   if (!c) return RFNSE_EINVAL;
   if (!u0 || nsteps < 0 || every < 1) {
     c->err = "rfnse_tape_forward: u0 required, nsteps >= 0, every >= 1";
@@ -220,6 +221,7 @@ int rfnse_tape_forward(rfnse_ctx* c, const void* u0, int nsteps, int every, void
 }
 
 int rfnse_tape_backward(rfnse_ctx* c, const void* gN, void* g0, double* grho, int* iters, int on_device) {
+  NvtxRange range("rfnse reverse pass");
   if (!c) return RFNSE_EINVAL;
   if (!gN || !g0 || c->tape_steps < 0) {
     c->err = "rfnse_tape_backward: needs gN, g0 and a taped run (rfnse_tape_forward)";

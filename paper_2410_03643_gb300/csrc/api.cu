@@ -1,6 +1,7 @@
 // C ABI (include/rfnse.h): context life cycle, state, time stepping and building blocks.
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -115,6 +116,7 @@ void free_ctx(rfnse_ctx* c) {
   }
   cudaFree(c->partials);
   cudaFree(c->counter);
+  cudaFree(c->dbg_count);
   cudaFree(c->gs);
   if (c->peek) cudaFreeHost(c->peek);
   for (cudaEvent_t ev : c->prof_events) cudaEventDestroy(ev);
@@ -285,7 +287,12 @@ int rfnse_create(const rfnse_params* p, void* stream, rfnse_ctx** out) {
     }
   }
   c->red_blocks = choose_reduce_blocks(N);
-  c->use_graphs = p->device_loop != 0;
+  {
+    const char* dbg = std::getenv("RFNSE_DEBUG");
+    c->debug = dbg && dbg[0] == '1';
+  }
+  c->use_graphs = p->device_loop != 0 && !c->debug;  // debug checks synchronise after every pass
+  if (c->debug) chk(dalloc(&c->dbg_count, 1));
   c->coop_blocks = coop_blocks_for(N);
   chk(dalloc(&c->bar, 1));
   chk(dalloc(&c->coop_partials, 2 * (size_t)c->coop_blocks));
@@ -392,7 +399,13 @@ int rfnse_run(rfnse_ctx* c, int nsteps, void* traj, int* iters, double* relres, 
   for (int s = 0; s < nsteps; ++s) {
     int it = 0;
     double rr = 0.0;
-    const rfnse_status st = time_step(c, &it, &rr);
+    NvtxRange range("rfnse step");
+    rfnse_status st = time_step(c, &it, &rr);
+    if (c->debug && !c->dbg_first.empty() && (st == RFNSE_OK || st == RFNSE_ENOCONV || st == RFNSE_ENUMERIC)) {
+      c->err = "debug check: first non-finite output after " + c->dbg_first;
+      c->dbg_first.clear();
+      st = RFNSE_ENUMERIC;
+    }
     if (st != RFNSE_OK && st != RFNSE_ENOCONV) return st;
     if (st == RFNSE_ENOCONV) worst = RFNSE_ENOCONV;
     if (iters) iters[s] = it;

@@ -7,10 +7,13 @@
 // host memory.  The three history slots form a ring (u^{n-1}, u^n, u^{n+1} in slots v, v+1, v+2 mod 3),
 // so there are three graphs, one per phase v, and a step moves no data.
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
 #include "internal.cuh"
+#include "lockstep.cuh"
+#include "passes.cuh"
 #include "solve.cuh"
 
 using namespace rfnse;
@@ -28,11 +31,27 @@ struct rfnse_batch {
   GmresPeek* h_peeks = nullptr;       // pinned
   std::vector<cudaEvent_t> events;
   std::string err;
+  // lock-step mode (lockstep.cuh): per step one graph whose every launch covers all instances
+  bool lockstep = false;
+  cudaStream_t cap2 = nullptr;          // captures the loop bodies of the lock-step graphs
+  cudaGraph_t lgraph[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t lexec[3] = {nullptr, nullptr, nullptr};
+  TableArena arena[3];                  // the batched launches' tables, one per ring phase
+  LockFlags* flags = nullptr;           // device, one per instance
+  GridBarrier* lbar = nullptr;          // barrier of the batched Arnoldi kernel
+  unsigned* done_all = nullptr;         // arrival counter of the batched kernels
+  unsigned long long* counts = nullptr;     // device: Arnoldi launches and cycles of the last step
+  unsigned long long* h_counts = nullptr;   // pinned copy
+  double* cpart = nullptr;              // partials of the batched Arnoldi kernel, 2 per block
+  int maxb = 0;                         // blocks of the batched Arnoldi kernel
+  long long arn_launches[3] = {0, 0, 0};  // batched pass launches per Arnoldi step, per phase graph
+  long long res_launches[3] = {0, 0, 0};  // ... per residual product
 };
 
 namespace {
 
 const double2 kOne = {1.0, 0.0};
+const double2 kMinusOne = {-1.0, 0.0};
 const double2 kMinusI = {0.0, -1.0};
 
 void free_batch(rfnse_batch* b) {
@@ -46,6 +65,18 @@ void free_batch(rfnse_batch* b) {
     if (s) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->events) cudaEventDestroy(e);
   if (b->cap) cudaStreamDestroy(b->cap);
+  for (int v = 0; v < 3; ++v) {
+    if (b->lexec[v]) cudaGraphExecDestroy(b->lexec[v]);
+    if (b->lgraph[v]) cudaGraphDestroy(b->lgraph[v]);
+    cudaFree(b->arena[v].dev);
+  }
+  if (b->cap2) cudaStreamDestroy(b->cap2);
+  cudaFree(b->flags);
+  cudaFree(b->lbar);
+  cudaFree(b->done_all);
+  cudaFree(b->counts);
+  if (b->h_counts) cudaFreeHost(b->h_counts);
+  cudaFree(b->cpart);
   cudaFree(b->d_gs);
   cudaFree(b->d_peeks);
   if (b->h_peeks) cudaFreeHost(b->h_peeks);
@@ -149,6 +180,250 @@ cudaError_t build_batch_graph(rfnse_batch* b, int v) {
   return cudaSuccess;
 }
 
+// Lock-step mode needs instances whose solves run the same kernels: the mixed form with the sine-transform
+// preconditioner, the same dimension, double-float residual products (every axis n + 1 in 128..1024),
+// at most 1024 instances and no more than the batched Arnoldi kernel's blocks.
+bool lockstep_eligible(const rfnse_batch* b) {
+  if (b->count < 1 || b->count > 1024) return false;
+  const int d = b->ctx[0]->d;
+  for (const rfnse_ctx* c : b->ctx)
+    if (c->p.precision != 1 || c->p.precond != 0 || c->d != d || !c->Tu[0] || !toeplitz_df_available(c))
+      return false;
+  return b->count <= ls_mgs_max_blocks();
+}
+
+cudaError_t lockstep_alloc(rfnse_batch* b) {
+  if (b->flags) return cudaSuccess;
+  const int n = b->count;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  b->maxb = ls_mgs_max_blocks();
+  chk(dev_alloc((void**)&b->flags, sizeof(LockFlags) * n));
+  chk(dev_alloc((void**)&b->lbar, sizeof(GridBarrier)));
+  chk(dev_alloc((void**)&b->done_all, sizeof(unsigned)));
+  chk(dev_alloc((void**)&b->counts, 2 * sizeof(unsigned long long)));
+  chk(host_alloc_pinned((void**)&b->h_counts, 2 * sizeof(unsigned long long)));
+  chk(dev_alloc((void**)&b->cpart, 2 * sizeof(double) * (size_t)b->maxb));
+  const size_t cap = 65536 + (size_t)n * 16384;  // LockInst + per pass launch a PassParams and an offset
+  for (int v = 0; v < 3; ++v) {
+    chk(dev_alloc((void**)&b->arena[v].dev, cap));
+    b->arena[v].cap = cap;
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMemset(b->flags, 0, sizeof(LockFlags) * n);
+  if (e == cudaSuccess) e = cudaMemset(b->lbar, 0, sizeof(GridBarrier));
+  if (e == cudaSuccess) e = cudaMemset(b->done_all, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(b->counts, 0, 2 * sizeof(unsigned long long));
+  return e;
+}
+
+// Record the lock-step graph of ring phase v: the set-up and solve start of all instances, the outer
+// (refinement) loop whose body starts a cycle, runs the inner (Arnoldi) loop, and updates every
+// instance's solution and residual, then the T u update and the statistics gather.  Each line pass of
+// an Arnoldi step or residual product is one launch per FFT length over every instance's tiles.
+cudaError_t build_lockstep_graph(rfnse_batch* b, int v) {
+  const int n = b->count;
+  cudaError_t e = lockstep_alloc(b);
+  if (e != cudaSuccess) return e;
+  TableArena& ar = b->arena[v];
+  ar.host.clear();
+  const int prev = v, cur = (v + 1) % 3, next = (v + 2) % 3;
+  // the batched Arnoldi kernel's blocks, shared in proportion to the instances' sizes
+  long long Ntot = 0;
+  for (rfnse_ctx* c : b->ctx) Ntot += c->N;
+  std::vector<int> ncb(n);
+  int sum = 0;
+  for (int i = 0; i < n; ++i) {
+    const long long N = b->ctx[i]->N;
+    long long want = (long long)((double)b->maxb * (double)N / (double)Ntot);
+    const long long need = (N + 255) / 256;
+    if (want > need) want = need;
+    if (want < 1) want = 1;
+    ncb[i] = (int)want;
+    sum += ncb[i];
+  }
+  while (sum > b->maxb) {  // at most maxb blocks (each instance keeps one)
+    int big = 0;
+    for (int i = 1; i < n; ++i)
+      if (ncb[i] > ncb[big]) big = i;
+    if (ncb[big] <= 1) return cudaErrorInvalidConfiguration;
+    --ncb[big];
+    --sum;
+  }
+  std::vector<LockInst> li(n);
+  long long blk = 0;
+  int cb = 0;
+  for (int i = 0; i < n; ++i) {
+    rfnse_ctx* c = b->ctx[i];
+    LockInst& I = li[i];
+    I.gs = c->gs;
+    I.fl = b->flags + i;
+    I.cfg = solve_cfg(c, 1);
+    I.N = c->N;
+    I.u_prev = c->u[prev];
+    I.u_cur = c->u[cur];
+    I.Tu_prev = c->Tu[prev];
+    I.x = c->u[next];
+    I.Tu_next = c->Tu[next];
+    I.f = c->f;
+    I.r = c->r;
+    I.w = c->w;
+    I.V = c->V;
+    I.Z32 = c->Z32;
+    I.D = c->D;
+    I.D32 = c->D32;
+    I.dfac64 = c->dfac64;
+    I.dfac32 = c->dfac32;
+    I.rho_dt = c->p.rho * c->p.dt;
+    I.omega = c->p.omega;
+    I.nrm_f = c->nrm_part;
+    I.nrm_df = c->nrm_part + kNormPartMax;
+    I.nrm_upd = c->nrm_part + 2 * kNormPartMax;
+    I.nb_df = 0;
+    I.dot_part = c->dot_part;
+    I.dot_n = 0;
+    I.blk0 = blk;
+    I.nblk = lock_ew_blocks(c->N);
+    blk += I.nblk;
+    I.cb0 = cb;
+    I.ncb = ncb[i];
+    I.cpart = b->cpart + 2 * (size_t)cb;
+    cb += ncb[i];
+  }
+  const long long blk_total = blk;
+  const int cb_total = cb;
+  // every instance's passes of one Arnoldi step and of one residual product, recorded, not launched
+  std::vector<std::vector<ParamRecord>> arn(n), res(n);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    rfnse_ctx* c = b->ctx[i];
+    double2* const x_own = c->x;
+    c->x = li[i].x;
+    c->param_rec = &arn[i];
+    e = record_mixed_arnoldi_passes(c, &b->flags[i].iskip);
+    c->param_rec = &res[i];
+    if (e == cudaSuccess)
+      e = run_matvec_fp64(c, c->x, c->D, c->r, c->f, kMinusOne, kMinusI, 0, &b->flags[i].dfskip, li[i].nrm_df);
+    c->param_rec = nullptr;
+    c->x = x_own;
+  }
+  if (e != cudaSuccess) return e;
+  for (int i = 1; i < n; ++i) {
+    if (arn[i].size() != arn[0].size() || res[i].size() != res[0].size()) return cudaErrorInvalidValue;
+    for (size_t k = 0; k < arn[0].size(); ++k)
+      if (arn[i][k].key != arn[0][k].key) return cudaErrorInvalidValue;
+    for (size_t k = 0; k < res[0].size(); ++k)
+      if (res[i][k].key != res[0][k].key) return cudaErrorInvalidValue;
+  }
+  LockInst* dli = static_cast<LockInst*>(ar.put(li.data(), sizeof(LockInst) * n));
+  if (!dli) return cudaErrorMemoryAllocation;
+  const size_t li_off = (size_t)((char*)dli - ar.dev);
+  // one batched launch per FFT length at pass position k; after() sees each member's tile count
+  long long launches = 0;
+  // one launch per FFT length at pass position k, one after another (each fills the GPU: measured faster
+  // than running a position's groups as parallel graph branches on the 64-instance workload)
+  auto launch_position = [&](std::vector<std::vector<ParamRecord>>& recs, size_t k, cudaStream_t s, bool last_arn,
+                             bool last_res) -> cudaError_t {
+    std::map<int, std::vector<int>> groups;
+    for (int i = 0; i < n; ++i) groups[recs[i][k].p.log2L].push_back(i);
+    for (auto& kv : groups) {
+      std::vector<PassParams> ps;
+      for (int i : kv.second) ps.push_back(recs[i][k].p);
+      std::vector<long long> grids;
+      int dot0 = 0;
+      const cudaError_t r = recs[kv.second[0]][k].group(ps, PassGeom{0, 0, 0}, ar, s, grids, &dot0);
+      if (r != cudaSuccess) return r;
+      ++launches;
+      for (size_t m = 0; m < kv.second.size(); ++m) {
+        LockInst& I = li[kv.second[m]];
+        if (last_arn) I.dot_n = dot0 ? (int)grids[m] : 0;
+        if (last_res) I.nb_df = ps[m].nrm_part ? (int)grids[m] : 0;
+      }
+    }
+    return cudaSuccess;
+  };
+  const long long launches_before = g_kernel_launches.load();  // capture records, it does not launch
+  cudaGraph_t g = nullptr;
+  cudaStream_t cs = b->cap, bs = b->cap2;
+  cudaGraphConditionalHandle ho = 0, hi = 0;
+  cudaGraph_t obody = nullptr, ibody = nullptr;
+  bool cs_open = false, bs_open = false;
+  e = cudaGraphCreate(&g, 0);
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  cs_open = e == cudaSuccess;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&ho, g, 0, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    launch_ls_step_prep(dli, n, blk_total, b->counts, cs);
+    launch_ls_norm_start(dli, n, b->lbar, b->done_all, ho, cs);
+    e = add_while_node(cs, ho, &obody);
+  }
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hi, obody, 0, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs, obody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  bs_open = e == cudaSuccess;
+  if (e == cudaSuccess) {  // outer body: one refinement cycle of every active instance
+    launch_ls_cycle_begin(dli, n, b->counts, hi, ho, bs);
+    e = add_while_node(bs, hi, &ibody);
+  }
+  if (e == cudaSuccess) {
+    launch_ls_backsolve(dli, n, bs);
+    launch_ls_combine_add(dli, n, blk_total, bs);
+    launch_ls_resid_coeffs(dli, n, bs);
+    launches = 0;
+    for (size_t k = 0; k < res[0].size() && e == cudaSuccess; ++k)
+      e = launch_position(res, k, bs, false, k + 1 == res[0].size());
+    b->res_launches[v] = launches;
+  }
+  if (e == cudaSuccess) {
+    launch_ls_resid_update(dli, n, blk_total, bs);
+    launch_ls_norm_resid(dli, n, b->done_all, ho, bs);
+  }
+  if (bs_open) {
+    const cudaError_t e2 = cudaStreamEndCapture(bs, &obody);
+    if (e == cudaSuccess) e = e2;
+    bs_open = false;
+  }
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  bs_open = e == cudaSuccess;
+  if (e == cudaSuccess) {  // inner body: one Arnoldi step of every instance still iterating
+    launches = 0;
+    for (size_t k = 0; k < arn[0].size() && e == cudaSuccess; ++k)
+      e = launch_position(arn, k, bs, k + 1 == arn[0].size(), false);
+    b->arn_launches[v] = launches;
+    if (e == cudaSuccess) e = launch_ls_mgs(dli, n, cb_total, b->lbar, b->done_all, b->counts, hi, bs);
+  }
+  if (bs_open) {
+    const cudaError_t e2 = cudaStreamEndCapture(bs, &ibody);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) {
+    launch_ls_tu(dli, n, blk_total, cs);
+    launch_gather_peeks(b->d_gs, b->d_peeks, n, cs);
+    e = cudaMemcpyAsync(b->h_peeks, b->d_peeks, sizeof(GmresPeek) * n, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->h_counts, b->counts, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, cs);
+  }
+  if (cs_open) {
+    cudaGraph_t out = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &out);
+    if (e == cudaSuccess) e = e2;
+  }
+  g_kernel_launches.store(launches_before);
+  if (e == cudaSuccess) {  // the tables with every instance's partial counts, then the graph
+    std::memcpy(ar.host.data() + li_off, li.data(), sizeof(LockInst) * n);
+    e = cudaMemcpy(ar.dev, ar.host.data(), ar.host.size(), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->lexec[v], g, 0);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    b->lexec[v] = nullptr;
+    cudaGetLastError();
+    return e;
+  }
+  b->lgraph[v] = g;
+  return cudaSuccess;
+}
+
 bool steady(const rfnse_ctx* c) { return c->step >= 1 && (c->p.precision == 0 || c->tu_valid[c->iprev]); }
 
 // Kernels one captured solve executed, from its statistics (as counted for stand-alone solves).
@@ -162,6 +437,8 @@ long long solve_kernels(const rfnse_ctx* c, const GmresPeek& pk) {
 }
 
 thread_local std::string g_batch_create_error;
+
+constexpr int kLockstepMinCount = 8;  // batches of at least this many eligible instances start in lock-step
 
 }  // namespace
 
@@ -211,9 +488,25 @@ int rfnse_batch_create(const rfnse_params* params, int count, void* stream, rfns
     free_batch(b);
     return st;
   }
+  // lock-step pays off for many instances (64 uneven 2-D instances: 8.3e8 -> 9.1e8 DOF.steps/s); a few
+  // large ones are faster as concurrent per-instance graphs (three 511^2: 8.9e8 against 7.1e8)
+  b->lockstep = count >= kLockstepMinCount && lockstep_eligible(b);
   *out = b;
   return RFNSE_OK;
 }
+
+int rfnse_batch_set_lockstep(rfnse_batch* b, int on) {
+  if (!b || (on != 0 && on != 1)) return RFNSE_EINVAL;
+  if (on && !lockstep_eligible(b)) {
+    b->err = "lock-step mode needs mixed-precision instances of one dimension with the sine-transform "
+             "preconditioner and n + 1 in 128..1024 on every axis";
+    return RFNSE_EINVAL;
+  }
+  b->lockstep = on != 0;
+  return RFNSE_OK;
+}
+
+int rfnse_batch_lockstep(const rfnse_batch* b) { return (b && b->lockstep) ? 1 : 0; }
 
 void rfnse_batch_destroy(rfnse_batch* b) {
   if (!b) return;
@@ -257,6 +550,7 @@ int rfnse_batch_run(rfnse_batch* b, int nsteps, int* iters, double* relres) {
   if (!b || nsteps < 0) return RFNSE_EINVAL;
   int worst = RFNSE_OK;
   for (int s = 0; s < nsteps; ++s) {
+    NvtxRange range("rfnse step");
     bool all_steady = true;
     for (rfnse_ctx* c : b->ctx) all_steady = all_steady && steady(c);
     // a failing instance does not stop the others' step: every instance takes this step (or fails it),
@@ -293,26 +587,32 @@ int rfnse_batch_run(rfnse_batch* b, int nsteps, int* iters, double* relres) {
         return RFNSE_ECUDA;
       }
     }
-    if (!b->exec[v]) {
-      const cudaError_t e = build_batch_graph(b, v);
+    cudaGraphExec_t* exec = b->lockstep ? &b->lexec[v] : &b->exec[v];
+    if (!*exec) {
+      const cudaError_t e = b->lockstep ? build_lockstep_graph(b, v) : build_batch_graph(b, v);
       if (e != cudaSuccess) {
-        b->err = std::string("batch graph: ") + cudaGetErrorString(e);
+        b->err = std::string(b->lockstep ? "lock-step graph: " : "batch graph: ") + cudaGetErrorString(e);
         return RFNSE_ECUDA;
       }
     }
-    cudaError_t e = cudaGraphLaunch(b->exec[v], b->stream);
+    cudaError_t e = cudaGraphLaunch(*exec, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    count_launch(1);  // the statistics gather
     if (e != cudaSuccess) {
       b->err = std::string("batch step: ") + cudaGetErrorString(e);
       return RFNSE_ECUDA;
+    }
+    if (b->lockstep) {  // every kernel of the graph ran for all instances: count them from the loop counts
+      const long long cycles = (long long)b->h_counts[1], steps = (long long)b->h_counts[0];
+      count_launch(2 + cycles * (1 + 3 + b->res_launches[v] + 2) + steps * (b->arn_launches[v] + 1) + 2);
+    } else {
+      count_launch(1);  // the statistics gather
     }
     for (int i = 0; i < b->count; ++i) {
       rfnse_ctx* c = b->ctx[i];
       const GmresPeek& pk = b->h_peeks[i];
       // set-up (mixed: one kernel; FP64: D, the product passes, the sub-solve tables), the solve,
       // and (mixed) T u from the final residual
-      count_launch(solve_kernels(c, pk) + (c->p.precision == 1 ? 2 : 2 + c->d));
+      if (!b->lockstep) count_launch(solve_kernels(c, pk) + (c->p.precision == 1 ? 2 : 2 + c->d));
       c->step += 1;
       c->iprev = (v + 1) % 3;
       c->icur = (v + 2) % 3;

@@ -5,71 +5,9 @@
 // handles these kernels set, a whole solve runs without the host.
 #include <cmath>
 #include "internal.cuh"
+#include "coop.cuh"
 
 namespace rfnse {
-
-constexpr int kCtlThreads = 256;
-constexpr unsigned long long kMaxSpin = 1ull << 22;  // bounded barrier wait (~0.3 s), then err = 1
-
-__device__ __forceinline__ double block_sum_c(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) sh[warp] = v;
-  __syncthreads();
-  v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
-  if (warp == 0)
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  __syncthreads();
-  return v;  // valid in thread 0
-}
-
-// Grid-wide barrier for a cooperative launch (all blocks co-resident).  The wait is bounded: after
-// kMaxSpin polls the block records the failure in *err and continues.
-__device__ __forceinline__ void grid_barrier_global(GridBarrier* b, int* err) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* vgen = &b->gen;
-    const unsigned g = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&b->count, 1u) + 1u;
-    if (arrived == gridDim.x) {
-      atomicExch(&b->count, 0u);
-      __threadfence();
-      atomicAdd(&b->gen, 1u);
-    } else {
-      unsigned long long spins = 0;
-      while (*vgen == g) {
-        if (++spins > kMaxSpin) {
-          *(volatile int*)err = 1;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-}
-
-// A one-block grid needs only the block barrier (uniform branch); larger grids use the global protocol.
-__device__ __forceinline__ void grid_barrier(GridBarrier* b, int* err) {
-  if (gridDim.x == 1) {
-    __syncthreads();
-    return;
-  }
-  grid_barrier_global(b, err);
-}
-
-// The same value in every block: the partials summed in a fixed order.
-__device__ __forceinline__ double fixed_sum(const double* part, int n, double* sh) {
-  double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) v += ((volatile const double*)part)[i];
-  v = block_sum_c(v, sh);
-  __shared__ double bc;
-  if (threadIdx.x == 0) bc = v;
-  __syncthreads();
-  return bc;
-}
 
 // Arnoldi step j = gs->j: w holds A M^{-1} v_j.  Modified Gram-Schmidt (for i = 0..j:
 // h_ij = <v_i, w>, w -= h_ij v_i; one pass per i fusing the previous subtraction with the next dot),
@@ -103,19 +41,8 @@ __global__ void __launch_bounds__(kCtlThreads) k_mgs_step(GmresState* gs, const 
     double* buf = partials + (size_t)(i & 1) * nb;
     const double2* vi = (i <= j) ? V + (size_t)i * ldv : nullptr;
     const double2* vp = (i > 0) ? V + (size_t)(i - 1) * ldv : nullptr;
-    double acc = 0.0;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (long long)nb * blockDim.x) {
-      double2 wv = w[k];
-      if (vp) {
-        const double2 pv = vp[k];
-        wv.x = fma(-hprev, pv.x, wv.x);
-        wv.y = fma(-hprev, pv.y, wv.y);
-        w[k] = wv;
-      }
-      const double2 a = vi ? vi[k] : wv;  // FMA chains: GB300 issues 2 FP64 FMAs per SM and cycle
-      acc = fma(a.x, wv.x, acc);
-      acc = fma(a.y, wv.y, acc);
-    }
+    double acc = mgs_sweep(w, vi, vp, hprev, N, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                           (long long)nb * blockDim.x);
     acc = block_sum_c(acc, sh);
     if (i == j + 1 && nb > 1) {
       // the norm: only one thread needs it, so the last block to arrive sums the partials and

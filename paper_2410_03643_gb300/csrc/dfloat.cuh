@@ -91,6 +91,9 @@ __device__ __forceinline__ cdf cscale(cdf a, dfl s) { return cdf{a.x * s, a.y * 
 __device__ __forceinline__ cdf cmul_i(cdf a) { return cdf{-a.y, a.x}; }
 __device__ __forceinline__ cdf cmul_mi(cdf a) { return cdf{a.y, -a.x}; }
 __device__ __forceinline__ cdf cdf_from(double2 v) { return cdf{df_split(v.x), df_split(v.y)}; }
+// storage of a complex double-float as (re.hi, re.lo, im.hi, im.lo)
+__device__ __forceinline__ cdf cdf_ld(float4 q) { return cdf{dfl(q.x, q.y), dfl(q.z, q.w)}; }
+__device__ __forceinline__ float4 cdf_st(cdf v) { return make_float4(v.x.hi, v.x.lo, v.y.hi, v.y.lo); }
 __device__ __forceinline__ double2 cdf_to(cdf v) { return make_double2(df_to_double(v.x), df_to_double(v.y)); }
 
 }  // namespace rfnse

@@ -2,8 +2,10 @@
 // shared between translation units.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <atomic>
 #include <cstdio>
+#include <cstring>
 #include <functional>
 #include <map>
 #include <string>
@@ -21,6 +23,15 @@ constexpr int kNormPartMax = 4096;  // largest grid whose squared-norm partials 
 // Number of kernels this library has launched in the process (all contexts).
 extern std::atomic<long long> g_kernel_launches;
 inline void count_launch(long long k = 1) { g_kernel_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// NVTX range for the span of a scope (time steps, solves, passes, the tuner), so that profilers can
+// group or select the kernels by what launched them (e.g. ncu --nvtx --nvtx-include "rfnse step/").
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Device and pinned-host allocations of contexts, batches and tapes go through these two (api.cu), so
 // that rfnse_test_fail_allocations can make them fail without exhausting the GPU's memory.
@@ -90,6 +101,26 @@ struct TuneRecord {
   std::vector<PassGeom> cands;
   std::function<cudaError_t(const PassGeom&)> launch;
 };
+
+// Device tables of batched launches (the lock-step batch): a device buffer and its host image, filled
+// while a graph is captured (the kernels only read them when the graph runs) and copied to the device
+// once the capture has ended.
+struct TableArena {
+  char* dev = nullptr;     // device buffer of cap bytes
+  size_t cap = 0;
+  std::vector<char> host;  // host image; host.size() bytes in use
+  // Reserve `bytes` (16-byte aligned), copy src into the host image, return the device address (null
+  // when the buffer is full).
+  void* put(const void* src, size_t bytes) {
+    const size_t off = (host.size() + 15) & ~(size_t)15;
+    if (off + bytes > cap) return nullptr;
+    host.resize(off + bytes);
+    if (bytes) std::memcpy(host.data() + off, src, bytes);
+    return dev + off;
+  }
+};
+
+struct ParamRecord;  // passes.cuh: a pass's parameters and its batched launcher (lock-step capture)
 
 // Counter and generation of a grid-wide barrier (control.cu); zero-initialised.
 struct GridBarrier {
@@ -166,11 +197,19 @@ void launch_step_prep(rfnse_ctx* c, const double2* uc, const double2* up, const 
 int step_prep_blocks(long long N);  // its grid (the number of partials it leaves)
 int resid_update_blocks(long long N);
 
+// Debug mode (rfnse_ctx::debug): after a line pass, wait for it and count the non-finite values among
+// `count` complex values of storage `elem` bytes each (8: float2, 16: double2) at each of the outputs;
+// the first pass with any is recorded in c->dbg_first with `what`.  Returns the launch or execution error.
+cudaError_t debug_after_pass(rfnse_ctx* c, cudaStream_t s, const char* what, const void* const* outs,
+                             const int* elems, int nout, long long count);
+
 // ---- double-float Toeplitz passes (toep_df.cu) --------------------------------------------------
 bool toeplitz_df_available(const rfnse_ctx* c);
+// dfz_in / dfz_out: the double-float copy of z shared by the passes of a product (float4 per point; see
+// PassParams), null when not used
 cudaError_t run_toeplitz_df(rfnse_ctx* c, int axis, int half, bool first, const double2* z, const double* D,
                             const double2* add, double2* w, double2 a, double2 b, const int* skip,
-                            double* nrm_part = nullptr);
+                            double* nrm_part = nullptr, const void* dfz_in = nullptr, void* dfz_out = nullptr);
 void launch_setup_df(int log2L, const double* c64h0, const double* c64h1, void* tw, void* c0, void* c1,
                      cudaStream_t s);
 
@@ -282,6 +321,14 @@ struct rfnse_ctx {
   std::map<unsigned long long, rfnse::PassGeom> tune;
   std::vector<rfnse::TuneRecord>* tune_rec = nullptr;
   long long tuned_launches = 0;  // pass launches whose geometry came from `tune`
+  // set only while a lock-step batch records this instance's pass sequence: the passes are recorded
+  // (parameters and batched launcher) instead of launched
+  std::vector<rfnse::ParamRecord>* param_rec = nullptr;
+  // debug mode (environment RFNSE_DEBUG=1 at rfnse_create): host-driven loops, every line pass checked
+  // after its launch (geometry covering the grid, launch and execution errors, non-finite outputs)
+  bool debug = false;
+  int* dbg_count = nullptr;        // device: non-finite values found by the last scan
+  std::string dbg_first;           // the first pass whose output had a non-finite value ("" if none)
   // kernel-class profiling (rfnse_profile): CUDA events around every launch of one pass kind
   int prof_kind = 0;
   std::vector<cudaEvent_t> prof_events;  // pairs (start, stop)

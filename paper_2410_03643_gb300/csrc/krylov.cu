@@ -4,6 +4,7 @@
 // are complex FP64 with the real inner product <a, b> = Re(a^H b), which is the Euclidean inner
 // product of the real block vectors [Im; Re] of Sec. 3.
 #include <cmath>
+#include <string>
 #include "internal.cuh"
 #include "cplx.cuh"
 
@@ -208,6 +209,49 @@ __global__ void k_step_prep(const double2* __restrict__ uc, const double2* __res
 __global__ void k_zero(double2* __restrict__ x, long long N) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
     x[i] = make_double2(0.0, 0.0);
+}
+
+// Count the non-finite components of n complex values (FP32 or FP64 storage) into *count.
+__global__ void k_count_nonfinite(const void* __restrict__ p, long long n, int is_double, int* count) {
+  int bad = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (is_double) {
+      const double2 v = reinterpret_cast<const double2*>(p)[i];
+      bad += !isfinite(v.x) || !isfinite(v.y);
+    } else {
+      const float2 v = reinterpret_cast<const float2*>(p)[i];
+      bad += !isfinite(v.x) || !isfinite(v.y);
+    }
+  }
+  if (bad) atomicAdd(count, bad);
+}
+
+cudaError_t debug_after_pass(rfnse_ctx* c, cudaStream_t s, const char* what, const void* const* outs,
+                             const int* elems, int nout, long long count) {
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    c->err = std::string("debug check after ") + what + ": " + cudaGetErrorString(e);
+    return e;
+  }
+  if (!c->dbg_count || !c->dbg_first.empty()) return cudaSuccess;
+  for (int k = 0; k < nout; ++k) {
+    if (!outs[k]) continue;
+    int h = 0;
+    e = cudaMemsetAsync(c->dbg_count, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+      k_count_nonfinite<<<152 * 4, 256, 0, s>>>(outs[k], count, elems[k] == 16, c->dbg_count);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, c->dbg_count, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    if (h > 0) {
+      c->dbg_first = std::string(what) + ": " + std::to_string(h) + " non-finite values in output " + std::to_string(k);
+      return cudaSuccess;
+    }
+  }
+  return cudaSuccess;
 }
 
 static inline unsigned ew_blocks(long long N) {

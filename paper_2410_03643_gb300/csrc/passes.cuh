@@ -97,6 +97,11 @@ struct PassParams {
   double* dot_part;
   // double-float Toeplitz passes: when set, each block's share of ||result||^2
   double* nrm_part;
+  // double-float Toeplitz passes of a product along several axes: the input split into double-float
+  // once, written by the first pass and read by the others (float4 per point: re.hi, re.lo, im.hi,
+  // im.lo); null when not used
+  const void* dfz_in;
+  void* dfz_out;
 };
 
 // Sum of v over the block, written by thread 0 to *out; every thread of the block must call it.  The
@@ -187,8 +192,37 @@ __device__ __forceinline__ void bluestein_lines(cv<R>* buf, int Lp, int L, int l
 constexpr int kPassMaxThreads = 512;  // the line-pass kernels' launch bound
 constexpr size_t kPassMaxSmem = 200 * 1024;  // the dynamic shared memory the pass kernels opt in to
 
+// A batched launch over several instances' tiles (the lock-step batch, lockstep.cu): block b works on
+// tile b - start[i] of instance i, start[i] <= b < start[i + 1], with that instance's parameters.
+struct PassWork {
+  const PassParams* plist;  // one per instance
+  const long long* start;   // n + 1 prefix sums of the instances' tile counts
+  int n;
+};
+
+// The work item of this block: its instance's parameters copied to shared memory and its tile there.
+__device__ __forceinline__ void pass_work_item(const PassWork& w, PassParams& ps, long long& tile) {
+  __shared__ int inst;
+  if (threadIdx.x == 0) {
+    const long long b = blockIdx.x;
+    int lo = 0, hi = w.n - 1;
+    while (lo < hi) {  // the last instance whose range starts at or before b
+      const int mid = (lo + hi + 1) >> 1;
+      if (w.start[mid] <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    inst = lo;
+    tile = b - w.start[lo];
+  }
+  __syncthreads();
+  const int* src = reinterpret_cast<const int*>(w.plist + inst);
+  int* dst = reinterpret_cast<int*>(&ps);
+  for (int i = threadIdx.x; i < (int)(sizeof(PassParams) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+}
+
 template <typename R, typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS, int LOG2L>
-__global__ void __launch_bounds__(kPassMaxThreads) k_line_pass(const PassParams p) {
+__device__ __forceinline__ void line_pass_body(const PassParams& p, const long long tile) {
   using V = cv<R>;
   if (p.skip && *p.skip) return;  // uniform: the whole launch is a no-op
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -207,10 +241,10 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_line_pass(const PassParams 
 
   long long line0 = 0, hi = 0, lo0 = 0;
   if (xax) {
-    line0 = (long long)blockIdx.x * B;
+    line0 = tile * B;
   } else {
-    hi = (long long)blockIdx.x / p.tiles_inner;
-    lo0 = ((long long)blockIdx.x - hi * p.tiles_inner) * B;
+    hi = tile / p.tiles_inner;
+    lo0 = (tile - hi * p.tiles_inner) * B;
   }
   // element e of the tile -> (line l, position pos), ordered for coalesced global access
   // (B is a power of two; a tile of x-lines of the large transforms is a single line)
@@ -417,8 +451,21 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_line_pass(const PassParams 
         dot = fma(v0.y, wv.y, dot);
       }
     }
-    if constexpr ((FLAGS & F_DOT0) != 0) block_sum_store(dot, p.dot_part + blockIdx.x);
+    if constexpr ((FLAGS & F_DOT0) != 0) block_sum_store(dot, p.dot_part + tile);
   }
+}
+
+template <typename R, typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS, int LOG2L>
+__global__ void __launch_bounds__(kPassMaxThreads) k_line_pass(const PassParams p) {
+  line_pass_body<R, TIN, TOUT, TACCI, TACCO, FLAGS, LOG2L>(p, blockIdx.x);
+}
+
+template <typename R, typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS, int LOG2L>
+__global__ void __launch_bounds__(kPassMaxThreads) k_line_pass_wl(const PassWork w) {
+  __shared__ PassParams ps;
+  __shared__ long long tile;
+  pass_work_item(w, ps, tile);
+  line_pass_body<R, TIN, TOUT, TACCI, TACCO, FLAGS, LOG2L>(ps, tile);
 }
 
 // FP32 passes whose FFT length is fixed at compile time (fixed_fft_length), every operation of
@@ -430,7 +477,7 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_line_pass(const PassParams 
 // global memory once rather than once per loop iteration and FFT stage; the twiddles are then staged in
 // shared memory, and z stays in registers between the sub-solve and the Toeplitz epilogue.
 template <typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS, int LOG2L>
-__global__ void __launch_bounds__(kPassMaxThreads) k_line_pass_fixed(const PassParams p) {
+__device__ __forceinline__ void line_pass_fixed_body(const PassParams& p, const long long tile) {
   static_assert(!(FLAGS & F_CIRC), "the circulant comparator's passes run in k_line_pass");
   static_assert(LOG2L > 0, "fixed FFT length only");
   static_assert(!(FLAGS & F_DOT0) || sizeof(TACCO) == sizeof(double2), "F_DOT0 needs an FP64 result");
@@ -453,10 +500,10 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_line_pass_fixed(const PassP
 
   long long line0 = 0, hi = 0, lo0 = 0;
   if (xax) {
-    line0 = (long long)blockIdx.x * B;
+    line0 = tile * B;
   } else {
-    hi = (long long)blockIdx.x / p.tiles_inner;
-    lo0 = ((long long)blockIdx.x - hi * p.tiles_inner) * B;
+    hi = tile / p.tiles_inner;
+    lo0 = (tile - hi * p.tiles_inner) * B;
   }
   // slot q of this thread: tile element e = tid + q B T -> line l, position pos, global index g
   int sl[QN], sp[QN];
@@ -694,8 +741,21 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_line_pass_fixed(const PassP
         dot = fma(v0q[q].y, (double)acc.y, dot);
       }
     }
-    if constexpr ((FLAGS & F_DOT0) != 0) block_sum_store(dot, p.dot_part + blockIdx.x);
+    if constexpr ((FLAGS & F_DOT0) != 0) block_sum_store(dot, p.dot_part + tile);
   }
+}
+
+template <typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS, int LOG2L>
+__global__ void __launch_bounds__(kPassMaxThreads) k_line_pass_fixed(const PassParams p) {
+  line_pass_fixed_body<TIN, TOUT, TACCI, TACCO, FLAGS, LOG2L>(p, blockIdx.x);
+}
+
+template <typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS, int LOG2L>
+__global__ void __launch_bounds__(kPassMaxThreads) k_line_pass_fixed_wl(const PassWork w) {
+  __shared__ PassParams ps;
+  __shared__ long long tile;
+  pass_work_item(w, ps, tile);
+  line_pass_fixed_body<TIN, TOUT, TACCI, TACCO, FLAGS, LOG2L>(ps, tile);
 }
 
 // Threads per line (one or two radix-4 butterflies each) and lines per block for FFT length L.
@@ -753,6 +813,43 @@ struct PassKernels {
       }
     }
     return k_line_pass<R, TIN, TOUT, TACCI, TACCO, FLAGS, 0>;
+  }
+  // the batched (work-list) kernels of the same configurations
+  using FnW = void (*)(const PassWork);
+  static FnW get_wl(int log2L, bool prefetch) {
+    if constexpr (sizeof(R) == 4 && (FLAGS & F_CIRC) == 0) {
+      if (prefetch) {
+        switch (log2L) {
+          case 8: return k_line_pass_fixed_wl<TIN, TOUT, TACCI, TACCO, FLAGS, 8>;
+          case 9: return k_line_pass_fixed_wl<TIN, TOUT, TACCI, TACCO, FLAGS, 9>;
+          case 10: return k_line_pass_fixed_wl<TIN, TOUT, TACCI, TACCO, FLAGS, 10>;
+          case 11: return k_line_pass_fixed_wl<TIN, TOUT, TACCI, TACCO, FLAGS, 11>;
+          default: break;
+        }
+      }
+    }
+    if constexpr (sizeof(R) == 4) {
+      switch (log2L) {
+        case 8: return k_line_pass_wl<R, TIN, TOUT, TACCI, TACCO, FLAGS, 8>;
+        case 9: return k_line_pass_wl<R, TIN, TOUT, TACCI, TACCO, FLAGS, 9>;
+        case 10: return k_line_pass_wl<R, TIN, TOUT, TACCI, TACCO, FLAGS, 10>;
+        case 11: return k_line_pass_wl<R, TIN, TOUT, TACCI, TACCO, FLAGS, 11>;
+        default: break;
+      }
+    }
+    return k_line_pass_wl<R, TIN, TOUT, TACCI, TACCO, FLAGS, 0>;
+  }
+  static cudaError_t allow_smem_wl() {
+    cudaError_t e = cudaSuccess;
+    for (int lg = 0; lg <= 12; ++lg) {
+      if (lg != 0 && !(sizeof(R) == 4 && fixed_fft_length(lg))) continue;
+      for (int pf = 0; pf < 2; ++pf) {
+        const cudaError_t r = cudaFuncSetAttribute(get_wl(lg, pf != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)kPassMaxSmem);
+        if (e == cudaSuccess) e = r;
+      }
+    }
+    return e;
   }
   // dynamic shared memory above 48 KB for every variant, once per process (thread-safe static init)
   static cudaError_t allow_smem() {
@@ -887,7 +984,19 @@ cudaError_t launch_pass_geom(rfnse_ctx* c, PassParams p, cudaStream_t s, const P
     c->prof_used += 2;
     cudaEventRecord(e0, s);
   }
-  kern<<<(unsigned)grid, p.B * p.nt, smem, s>>>(p);
+  if (c->debug) {  // the tiles must cover the grid's lines exactly once
+    const long long covered = xax ? grid * p.B : p.tiles_inner * p.B * (p.nlines / p.stride);
+    const long long spare = xax ? (grid - 1) * p.B : (p.tiles_inner - 1) * p.B * (p.nlines / p.stride);
+    if (p.nlines * p.n != c->N || covered < p.nlines || spare >= p.nlines ||
+        (!xax && p.nlines % p.stride != 0)) {
+      c->err = "debug check: line-pass geometry does not cover the grid";
+      return cudaErrorInvalidConfiguration;
+    }
+  }
+  {
+    NvtxRange range("rfnse pass");
+    kern<<<(unsigned)grid, p.B * p.nt, smem, s>>>(p);
+  }
   count_launch();
   if (prof) {
     cudaEventRecord(e1, s);
@@ -895,6 +1004,18 @@ cudaError_t launch_pass_geom(rfnse_ctx* c, PassParams p, cudaStream_t s, const P
     pass_work<R, TIN, TOUT, TACCI, TACCO, FLAGS>(p, fl, by);
     c->prof_flops += fl;
     c->prof_bytes += by;
+  }
+  cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+  if (c->debug && cudaStreamIsCapturing(s, &cap_st) == cudaSuccess && cap_st == cudaStreamCaptureStatusNone) {
+    char what[96];
+    std::snprintf(what, sizeof what, "line pass (flags %d, %s, axis stride %lld)", FLAGS,
+                  sizeof(R) == 4 ? "FP32" : "FP64", p.stride);
+    const void* outs[3] = {(FLAGS & (F_DST | F_DSCALE)) ? p.out : nullptr,
+                           (FLAGS & (F_TOEP_X | F_TOEP_ACC)) ? p.acc_out : nullptr,
+                           (FLAGS & F_INSCALE) ? (const void*)p.copy_out : nullptr};
+    const int elems[3] = {(int)sizeof(TOUT), (int)sizeof(TACCO), 16};
+    if (p.gdyn) outs[0] = outs[2] = nullptr;  // device-resolved operands: not known on the host
+    return debug_after_pass(c, s, what, outs, elems, 3, c->N);
   }
   return cudaGetLastError();
 }
@@ -927,10 +1048,125 @@ std::vector<PassGeom> pass_candidates(const PassParams& p, bool fixed, size_t el
   return out;
 }
 
+// A pass of one instance recorded for a lock-step batch: its key, parameters and geometry, and the
+// launcher of the batched kernel for a group of instances that run the same pass with the same FFT
+// length.  grids receives every member's tile count; *dot0 whether the partials of <v_0, w> were
+// written (F_DOT0 passes; 0 when some member's grid is too large for the Arnoldi kernel to sum).
+struct ParamRecord {
+  unsigned long long key = 0;
+  PassParams p{};
+  PassGeom geom{};
+  bool df = false;  // double-float residual pass (toep_df.cu)
+  std::function<cudaError_t(std::vector<PassParams>&, const PassGeom&, TableArena&, cudaStream_t,
+                            std::vector<long long>&, int*)>
+      group;
+};
+
+// The geometry of a batched launch over instances with the same FFT length on this axis: the default
+// tile for the combined number of lines (on strided axes at most the smallest stride), the prefetching
+// kernel while the combined grid stays within about four waves.
+template <int FLAGS>
+PassGeom group_pass_geometry(const std::vector<PassParams>& ps, bool fixed) {
+  const PassParams& p0 = ps[0];
+  const bool xax = (p0.stride == 1);
+  long long avail = xax ? 0 : (1LL << 62), lines = 0;
+  for (const PassParams& p : ps) {
+    lines += p.nlines;
+    if (xax) avail += p.nlines;
+    else if (p.stride < avail) avail = p.stride;
+  }
+  PassGeom g{};
+  if (fixed) pass_geometry_fixed(p0.L, xax, avail, lines, g.nt, g.B);
+  else pass_geometry(p0.L, xax, avail, g.nt, g.B);
+  long long grid = 0;
+  for (const PassParams& p : ps)
+    grid += xax ? (p.nlines + g.B - 1) / g.B : ((p.stride + g.B - 1) / g.B) * (p.nlines / p.stride);
+  g.variant = (fixed && !(FLAGS & F_CIRC) && grid <= 4 * 152) ? 1 : 0;
+  return g;
+}
+
+// One batched launch of a pass over a group of instances (same configuration and FFT length): block b
+// runs tile b - start[i] of member i.  The members' parameter blocks and tile offsets go into the
+// arena.  Geometry gin (gin.B = 0: group_pass_geometry), checked as in launch_pass_geom.
+template <typename R, typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS>
+cudaError_t launch_pass_group(std::vector<PassParams>& ps, const PassGeom& gin, TableArena& ar, cudaStream_t s,
+                              std::vector<long long>& grids, int* dot0) {
+  using V = cv<R>;
+  if (ps.empty()) return cudaSuccess;
+  const int L = ps[0].L;
+  const bool fixed = sizeof(R) == 4 && fixed_fft_length(ps[0].log2L);
+  const PassGeom g = gin.B > 0 ? gin : group_pass_geometry<FLAGS>(ps, fixed);  // B = 0: the default
+  const bool prefetch = fixed && !(FLAGS & F_CIRC) && g.variant == 1;
+  if (g.B < 1 || (g.B & (g.B - 1)) != 0 || g.B * g.nt > kPassMaxThreads || g.B * g.nt < 1)
+    return cudaErrorInvalidConfiguration;
+  if (fixed ? (g.nt != (L >> kFixedLogR)) : (g.nt != L / 4 && g.nt != L / 8)) return cudaErrorInvalidConfiguration;
+  std::vector<long long> start(ps.size() + 1, 0);
+  grids.assign(ps.size(), 0);
+  bool dot_fits = true;
+  for (size_t i = 0; i < ps.size(); ++i) {
+    PassParams& p = ps[i];
+    if (p.L != L) return cudaErrorInvalidValue;
+    p.B = g.B;
+    p.nt = g.nt;
+    p.dst_scale_f = (float)p.dst_scale;
+    p.ca_f = make_float2((float)p.ca.x, (float)p.ca.y);
+    p.cb_f = make_float2((float)p.cb.x, (float)p.cb.y);
+    p.log2B = 0;
+    while ((1 << p.log2B) < p.B) ++p.log2B;
+    long long grid;
+    if (p.stride == 1) {
+      grid = (p.nlines + p.B - 1) / p.B;
+      p.tiles_inner = 1;
+    } else {
+      p.tiles_inner = (p.stride + p.B - 1) / p.B;
+      grid = p.tiles_inner * (p.nlines / p.stride);
+    }
+    grids[i] = grid;
+    start[i + 1] = start[i] + grid;
+    if (grid > kDot0MaxBlocks) dot_fits = false;
+  }
+  if constexpr ((FLAGS & F_DOT0) != 0) {
+    if (!dot_fits) {
+      if (dot0) *dot0 = 0;
+      return launch_pass_group<R, TIN, TOUT, TACCI, TACCO, FLAGS & ~F_DOT0>(ps, g, ar, s, grids, nullptr);
+    }
+    if (dot0) *dot0 = 1;
+  }
+  size_t smem = ((size_t)g.B * fft_line_stride(L) + ((fixed && !prefetch) ? 0 : L)) * sizeof(V);
+  if ((FLAGS & F_TOEP_X) && !prefetch) smem += (size_t)g.B * ps[0].n * sizeof(V);
+  if (smem > kPassMaxSmem) return cudaErrorInvalidConfiguration;
+  if (start.back() <= 0) return cudaSuccess;
+  using K = PassKernels<R, TIN, TOUT, TACCI, TACCO, FLAGS>;
+  static const cudaError_t attr_err = K::allow_smem_wl();
+  if (attr_err != cudaSuccess) return attr_err;
+  const void* dp = ar.put(ps.data(), sizeof(PassParams) * ps.size());
+  const void* ds = ar.put(start.data(), sizeof(long long) * start.size());
+  if (!dp || !ds) return cudaErrorMemoryAllocation;
+  PassWork w{static_cast<const PassParams*>(dp), static_cast<const long long*>(ds), (int)ps.size()};
+  {
+    NvtxRange range("rfnse pass group");
+    K::get_wl(fixed ? ps[0].log2L : 0, prefetch)<<<(unsigned)start.back(), g.B * g.nt, smem, s>>>(w);
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <typename R, typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS>
 cudaError_t launch_pass(rfnse_ctx* c, PassParams p, cudaStream_t s) {
   const bool fixed = sizeof(R) == 4 && fixed_fft_length(p.log2L);
   PassGeom g = default_pass_geometry<FLAGS>(p, fixed);
+  if (c->param_rec) {  // a lock-step batch records the pass instead of launching it
+    ParamRecord r;
+    r.key = pass_key<R, TIN, TOUT, TACCI, TACCO, FLAGS>(c, p);
+    r.p = p;
+    r.geom = g;
+    r.group = [](std::vector<PassParams>& ps, const PassGeom& gg, TableArena& ar, cudaStream_t st,
+                 std::vector<long long>& grids, int* dot0) {
+      return launch_pass_group<R, TIN, TOUT, TACCI, TACCO, FLAGS>(ps, gg, ar, st, grids, dot0);
+    };
+    c->param_rec->push_back(std::move(r));
+    return cudaSuccess;
+  }
   if (c->tune_rec || !c->tune.empty()) {
     const unsigned long long key = pass_key<R, TIN, TOUT, TACCI, TACCO, FLAGS>(c, p);
     if (c->tune_rec) {  // rfnse_autotune is recording the solver's pass configurations

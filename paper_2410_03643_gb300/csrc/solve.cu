@@ -55,13 +55,17 @@ cudaError_t run_matvec_fp64(rfnse_ctx* c, const double2* z, const double* D, dou
   const int h = half ? 1 : 0;
   c->nrm_df_blocks = 0;
   if (c->p.precision == 1 && toeplitz_df_available(c)) {
-    // the last pass may leave the partials of ||w||^2 (c->nrm_df_blocks of them)
-    if ((e = run_toeplitz_df(c, 0, h, true, z, D, add, w, a, b, skip, c->d == 1 ? nrm_part : nullptr)) !=
+    // the last pass may leave the partials of ||w||^2 (c->nrm_df_blocks of them).  With several axes the
+    // first pass splits z into double-float once, into the FP64 work vector t1 (16 bytes per point,
+    // unused by the mixed form while a product runs), and the others read the split copy
+    const bool multi = c->d > 1;
+    void* zdf = multi ? (void*)c->t1 : nullptr;
+    if ((e = run_toeplitz_df(c, 0, h, true, z, D, add, w, a, b, skip, multi ? nullptr : nrm_part, nullptr, zdf)) !=
         cudaSuccess)
       return e;
     for (int a2 = 1; a2 < c->d; ++a2)
-      if ((e = run_toeplitz_df(c, a2, h, false, z, nullptr, w, w, a, b, skip,
-                               a2 == c->d - 1 ? nrm_part : nullptr)) != cudaSuccess)
+      if ((e = run_toeplitz_df(c, a2, h, false, z, nullptr, w, w, a, b, skip, a2 == c->d - 1 ? nrm_part : nullptr,
+                               zdf, nullptr)) != cudaSuccess)
         return e;
     return cudaSuccess;
   }
@@ -132,6 +136,22 @@ static SolveCfg make_cfg(const rfnse_ctx* c, int mixed) {
   cfg.tol = c->p.tol;
   cfg.eta_min = c->p.inner_tol > 0 ? c->p.inner_tol : 1e-6;
   return cfg;
+}
+
+SolveCfg solve_cfg(const rfnse_ctx* c, int mixed) { return make_cfg(c, mixed); }
+
+// The line passes of one Arnoldi step of the mixed form with device-resolved operands (as the solve
+// graphs launch them), recorded for a lock-step batch (c->param_rec set) with the given skip flag.
+cudaError_t record_mixed_arnoldi_passes(rfnse_ctx* c, const int* skip) {
+  Dyn dyn;
+  dyn.gs = c->gs;
+  dyn.vbase = c->V;
+  dyn.zbase = c->Z32;
+  dyn.ldv = c->N;
+  dyn.skip = skip;
+  dyn.dot0 = true;
+  return run_precon<float, double2, float2, float2, float2, true, true>(
+      c, nullptr, nullptr, nullptr, c->Z32, 0, c->D, c->w, c->wp32, nullptr, kOne, kI, 0, c->t1f, c->t2f, dyn);
 }
 
 // Host-driven Arnoldi steps: operands from the host, but the last product pass leaves the partials of
@@ -328,7 +348,7 @@ static rfnse_status solve_mixed(rfnse_ctx* c, const double* D, const double2* f,
 
 // Add a conditional WHILE node at the current capture position of stream s and make it the capture's
 // dependency; returns its body graph.
-static cudaError_t add_while_node(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+cudaError_t add_while_node(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body) {
   cudaStreamCaptureStatus st;
   cudaGraph_t g = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -506,6 +526,7 @@ static rfnse_status solve_graph(rfnse_ctx* c, const double* D, const double2* f,
 
 rfnse_status solve_block(rfnse_ctx* c, const double* D, const double2* f, double2* x, int half, int* iters,
                          double* relres) {
+  NvtxRange range("rfnse solve");
   int outer = 0;
   rfnse_status st;
   if (c->use_graphs) {
@@ -706,6 +727,7 @@ cudaError_t record_solver_passes(rfnse_ctx* c, std::vector<TuneRecord>* rec) {
 }  // namespace
 
 rfnse_status autotune(rfnse_ctx* c, int reps, int force, int* n_configs, int* n_changed, double* est_speedup) {
+  NvtxRange range("rfnse autotune");
   int dev = 0;
   RFNSE_CUDA_TRY(c, cudaGetDevice(&dev));
   std::vector<TuneRecord> rec;

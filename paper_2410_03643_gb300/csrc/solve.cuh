@@ -19,6 +19,12 @@ rfnse_status tban_solve(rfnse_ctx* c, const double* D, const double2* f, double2
                         double* relres);
 cudaError_t prepare_D(rfnse_ctx* c, const double* D);
 // f_part / f_n: block partials of ||f||^2 left by f's producer in the same graph (f_n = 0: none)
+// the settings of c's solves (mixed = 1: the mixed form)
+SolveCfg solve_cfg(const rfnse_ctx* c, int mixed);
+// a conditional WHILE node at the capture position of s, made the capture's dependency; its body graph
+cudaError_t add_while_node(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body);
+// lock-step batches: record (c->param_rec) the passes of one mixed-form Arnoldi step, skipped when *skip
+cudaError_t record_mixed_arnoldi_passes(rfnse_ctx* c, const int* skip);
 // rfnse_autotune: tune the geometry of every line-pass configuration of c's solves (reps timed launches
 // per candidate; force = 1 ignores choices made for the same grid by other contexts)
 rfnse_status autotune(rfnse_ctx* c, int reps, int force, int* n_configs, int* n_changed, double* est_speedup);

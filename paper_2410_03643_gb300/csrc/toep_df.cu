@@ -36,7 +36,7 @@ static int coef_code(double2 c) {
 }
 
 template <int LOG2L, bool FIRST>
-__global__ void __launch_bounds__(kPassMaxThreads) k_toeplitz_df(const PassParams p) {
+__device__ __forceinline__ void toeplitz_df_body(const PassParams& p, const long long tile) {
   using V = cdf;
   if (p.skip && *p.skip) return;  // uniform
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -51,10 +51,10 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_toeplitz_df(const PassParam
 
   long long line0 = 0, hi = 0, lo0 = 0;
   if (xax) {
-    line0 = (long long)blockIdx.x * B;
+    line0 = tile * B;
   } else {
-    hi = (long long)blockIdx.x / p.tiles_inner;
-    lo0 = ((long long)blockIdx.x - hi * p.tiles_inner) * B;
+    hi = tile / p.tiles_inner;
+    lo0 = (tile - hi * p.tiles_inner) * B;
   }
   // the tiling of k_line_pass: x lines contiguous, strided tiles of B lines adjacent in x
   auto map = [&](int e, int& l, int& pos) {
@@ -78,14 +78,26 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_toeplitz_df(const PassParam
   };
   auto at = [&](int l, int i) -> V& { return buf[(size_t)l * Lp + fft_pad(i)]; };
 
-  // load z into positions 1..n of the embedding, zero the rest
+  // load z into positions 1..n of the embedding, zero the rest.  In a product along several axes the
+  // first pass splits z into double-float and leaves the split copy for the others (FP64 work saved)
   const double2* in = reinterpret_cast<const double2*>(p.in);
+  const float4* zdf_in = reinterpret_cast<const float4*>(p.dfz_in);
+  float4* zdf_out = reinterpret_cast<float4*>(p.dfz_out);
   for (int e = tid; e < B * n; e += nthr) {
     int l, pos;
     map(e, l, pos);
     bool valid;
     const long long g = gidx(l, pos, valid);
-    at(l, 1 + pos) = valid ? cdf_from(in[g]) : zero;
+    cdf v = zero;
+    if (valid) {
+      if (zdf_in) {
+        v = cdf_ld(zdf_in[g]);
+      } else {
+        v = cdf_from(in[g]);
+        if (zdf_out) zdf_out[g] = cdf_st(v);
+      }
+    }
+    at(l, 1 + pos) = v;
   }
   for (int e = tid; e < B * Nh; e += nthr) {  // positions 0 and n+1 .. L-1 (n + 1 = L/2)
     const int l = e / Nh, k = e - l * Nh;
@@ -104,10 +116,13 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_toeplitz_df(const PassParam
   __syncthreads();
   fft_lines_fixed<LOG2L, kFixedLogRDF, true, false, true>(buf, Lp, B, tw);    // lower half out
 
-  // epilogue in FP64: FIRST acc = add + a z + b (t - D z); otherwise acc = acc + b t
+  // epilogue in FP64: FIRST acc = add + a z + b (t - D z); otherwise acc = acc + b t.  The block
+  // partials of ||result||^2 only where asked for (the last pass of a product): two FP64 FMAs per point
+  // less elsewhere (GB300's FP64 pipe issues 1/64 of the FP32 rate, and it bounds these passes)
   const double2* accin = reinterpret_cast<const double2*>(p.acc_in);
   double2* accout = reinterpret_cast<double2*>(p.acc_out);
   const double* D = reinterpret_cast<const double*>(p.Dr);
+  const bool want_nrm = p.nrm_part != nullptr;
   double nacc = 0.0;
   for (int e = tid; e < B * n; e += nthr) {
     int l, pos;
@@ -126,10 +141,26 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_toeplitz_df(const PassParam
     }
     const double2 out = cadd(acc, coef_mul(p.cb_code, p.cb, t));
     accout[g] = out;
-    nacc = fma(out.x, out.x, nacc);
-    nacc = fma(out.y, out.y, nacc);
+    if (want_nrm) {
+      nacc = fma(out.x, out.x, nacc);
+      nacc = fma(out.y, out.y, nacc);
+    }
   }
-  if (p.nrm_part) block_sum_store(nacc, p.nrm_part + blockIdx.x);  // share of ||result||^2 (uniform)
+  if (want_nrm) block_sum_store(nacc, p.nrm_part + tile);  // share of ||result||^2 (uniform)
+}
+
+template <int LOG2L, bool FIRST>
+__global__ void __launch_bounds__(kPassMaxThreads) k_toeplitz_df(const PassParams p) {
+  toeplitz_df_body<LOG2L, FIRST>(p, blockIdx.x);
+}
+
+// batched over several instances' tiles (lock-step batch), as k_line_pass_wl
+template <int LOG2L, bool FIRST>
+__global__ void __launch_bounds__(kPassMaxThreads) k_toeplitz_df_wl(const PassWork w) {
+  __shared__ PassParams ps;
+  __shared__ long long tile;
+  pass_work_item(w, ps, tile);
+  toeplitz_df_body<LOG2L, FIRST>(ps, tile);
 }
 
 template <int LOG2L>
@@ -150,6 +181,87 @@ static cudaError_t launch_df(rfnse_ctx* c, const PassParams& p, bool first, size
   return cudaGetLastError();
 }
 
+template <int LOG2L>
+static cudaError_t launch_df_wl(const PassWork& w, bool first, size_t smem, unsigned grid, int threads,
+                                cudaStream_t s) {
+  auto kern = first ? k_toeplitz_df_wl<LOG2L, true> : k_toeplitz_df_wl<LOG2L, false>;
+  static const cudaError_t attr =
+      [] {
+        cudaError_t e1 = cudaFuncSetAttribute(k_toeplitz_df_wl<LOG2L, true>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaError_t e2 = cudaFuncSetAttribute(k_toeplitz_df_wl<LOG2L, false>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        return e1 != cudaSuccess ? e1 : e2;
+      }();
+  if (attr != cudaSuccess) return attr;
+  {
+    NvtxRange range("rfnse pass group");
+    kern<<<grid, threads, smem, s>>>(w);
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Tile geometry of a double-float pass for nlines lines with `avail` lines adjacent (x: all).
+static void df_geometry(PassParams& p, long long avail, long long nlines) {
+  const bool xax = (p.stride == 1);
+  pass_geometry_fixed(p.L, xax, avail, nlines, p.nt, p.B, kFixedLogRDF);
+  p.log2B = 0;
+  while ((1 << p.log2B) < p.B) ++p.log2B;
+}
+
+// Batched double-float pass over a group of instances with the same FFT length on this axis (the
+// lock-step batch's residual products).  A member whose grid is too large for its norm partials gets
+// nrm_part = null (grids[i] still reports its tile count).
+static cudaError_t launch_df_group(std::vector<PassParams>& ps, bool first, TableArena& ar, cudaStream_t s,
+                                   std::vector<long long>& grids) {
+  if (ps.empty()) return cudaSuccess;
+  const bool xax = (ps[0].stride == 1);
+  long long avail = xax ? 0 : (1LL << 62), lines = 0;
+  for (const PassParams& p : ps) {
+    lines += p.nlines;
+    if (xax) avail += p.nlines;
+    else if (p.stride < avail) avail = p.stride;
+  }
+  PassParams g = ps[0];
+  df_geometry(g, avail, lines);
+  if (g.B * g.nt > kPassMaxThreads || g.B * g.nt < 1) return cudaErrorInvalidConfiguration;
+  std::vector<long long> start(ps.size() + 1, 0);
+  grids.assign(ps.size(), 0);
+  for (size_t i = 0; i < ps.size(); ++i) {
+    PassParams& p = ps[i];
+    if (p.L != g.L) return cudaErrorInvalidValue;
+    p.B = g.B;
+    p.nt = g.nt;
+    p.log2B = g.log2B;
+    long long grid;
+    if (p.stride == 1) {
+      grid = (p.nlines + p.B - 1) / p.B;
+      p.tiles_inner = 1;
+    } else {
+      p.tiles_inner = (p.stride + p.B - 1) / p.B;
+      grid = p.tiles_inner * (p.nlines / p.stride);
+    }
+    if (p.nrm_part && grid > kNormPartMax) p.nrm_part = nullptr;
+    grids[i] = grid;
+    start[i + 1] = start[i] + grid;
+  }
+  if (start.back() <= 0) return cudaSuccess;
+  const void* dp = ar.put(ps.data(), sizeof(PassParams) * ps.size());
+  const void* ds = ar.put(start.data(), sizeof(long long) * start.size());
+  if (!dp || !ds) return cudaErrorMemoryAllocation;
+  const PassWork w{static_cast<const PassParams*>(dp), static_cast<const long long*>(ds), (int)ps.size()};
+  const size_t smem = (size_t)g.B * fft_line_stride(g.L) * sizeof(cdf);
+  const unsigned grid = (unsigned)start.back();
+  switch (g.log2L) {
+    case 8: return launch_df_wl<8>(w, first, smem, grid, g.B * g.nt, s);
+    case 9: return launch_df_wl<9>(w, first, smem, grid, g.B * g.nt, s);
+    case 10: return launch_df_wl<10>(w, first, smem, grid, g.B * g.nt, s);
+    case 11: return launch_df_wl<11>(w, first, smem, grid, g.B * g.nt, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 bool toeplitz_df_available(const rfnse_ctx* c) {
   if (!c->twdf[0]) return false;
   for (int a = 0; a < c->d; ++a)
@@ -160,8 +272,10 @@ bool toeplitz_df_available(const rfnse_ctx* c) {
 // One Toeplitz pass along `axis` in double-float: first = the x-pass with diagonal and coupling.
 cudaError_t run_toeplitz_df(rfnse_ctx* c, int axis, int half, bool first, const double2* z, const double* D,
                             const double2* add, double2* w, double2 a, double2 b, const int* skip,
-                            double* nrm_part) {
+                            double* nrm_part, const void* dfz_in, void* dfz_out) {
   PassParams p{};
+  p.dfz_in = dfz_in;
+  p.dfz_out = dfz_out;
   p.n = c->n[axis];
   p.L = c->L[axis];
   p.log2L = c->log2L[axis];
@@ -179,9 +293,18 @@ cudaError_t run_toeplitz_df(rfnse_ctx* c, int axis, int half, bool first, const 
   p.cb_code = coef_code(b);
   p.skip = skip;
   const bool xax = (p.stride == 1);
-  pass_geometry_fixed(p.L, xax, xax ? p.nlines : p.stride, p.nlines, p.nt, p.B, kFixedLogRDF);
-  p.log2B = 0;
-  while ((1 << p.log2B) < p.B) ++p.log2B;
+  if (c->param_rec) {  // a lock-step batch records the pass instead of launching it
+    ParamRecord r;
+    r.key = (first ? F_TOEP_X : F_TOEP_ACC) | RFNSE_K_DF | ((unsigned long long)axis << 13);
+    p.nrm_part = nrm_part;
+    r.p = p;
+    r.df = true;
+    r.group = [first](std::vector<PassParams>& ps, const PassGeom&, TableArena& ar, cudaStream_t st,
+                      std::vector<long long>& grids, int*) { return launch_df_group(ps, first, ar, st, grids); };
+    c->param_rec->push_back(std::move(r));
+    return cudaSuccess;
+  }
+  df_geometry(p, xax ? p.nlines : p.stride, p.nlines);
   long long grid;
   if (xax) {
     grid = (p.nlines + p.B - 1) / p.B;
@@ -221,11 +344,21 @@ cudaError_t run_toeplitz_df(rfnse_ctx* c, int axis, int half, bool first, const 
     case 11: e = launch_df<11>(c, p, first, smem, (unsigned)grid, p.B * p.nt, c->stream); break;
     default: return cudaErrorInvalidValue;
   }
+  cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+  if (e == cudaSuccess && c->debug && cudaStreamIsCapturing(c->stream, &cap_st) == cudaSuccess &&
+      cap_st == cudaStreamCaptureStatusNone) {  // debug mode: the result (or its double-float running sum)
+    const void* outs[1] = {w};
+    const int elems[1] = {16};
+    e = debug_after_pass(c, c->stream, first ? "double-float Toeplitz pass (first axis)" : "double-float Toeplitz pass",
+                         outs, elems, 1, c->N);
+  }
   if (prof) {
     cudaEventRecord(e1, c->stream);
     const double lines = (double)p.nlines, N = lines * p.n;
     c->prof_flops += lines * 2.0 * 5.0 * p.L * p.log2L;  // two FFTs of length L per line
-    c->prof_bytes += N * (16.0 + 16.0 + (add ? 16.0 : 0.0) + ((first && D) ? 8.0 : 0.0));
+    // z (or its double-float copy) in, the result out, the additive vector or running sum in, D in; the
+    // first pass of a product along several axes also stores z split
+    c->prof_bytes += N * (16.0 + 16.0 + (add ? 16.0 : 0.0) + ((first && D) ? 8.0 : 0.0) + (dfz_out ? 16.0 : 0.0));
   }
   return e;
 }

@@ -58,7 +58,8 @@ EXPORTED = ("rfnse_default_params", "rfnse_create", "rfnse_destroy", "rfnse_last
             "rfnse_batch_destroy", "rfnse_batch_last_error", "rfnse_batch_context", "rfnse_batch_run",
             "rfnse_tape_forward", "rfnse_tape_backward", "rfnse_adjoint_solve", "rfnse_tban_solve",
             "rfnse_selftest_bounded_wait", "rfnse_test_fail_allocations", "rfnse_apply_prec_static",
-            "rfnse_autotune", "rfnse_tuned_launches", "rfnse_batch_autotune")
+            "rfnse_autotune", "rfnse_tuned_launches", "rfnse_batch_autotune", "rfnse_batch_set_lockstep",
+            "rfnse_batch_lockstep")
 
 K_INSCALE, K_DST, K_LAM, K_DSCALE, K_TOEP_X, K_TOEP_ACC, K_FP32, K_DF, K_ARNOLDI = 1, 2, 4, 8, 16, 32, 256, 1024, 2048
 
@@ -139,6 +140,10 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.rfnse_tuned_launches.restype = ctypes.c_longlong
     lib.rfnse_batch_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.rfnse_batch_autotune.restype = ip
+    lib.rfnse_batch_set_lockstep.argtypes = [vp, ip]
+    lib.rfnse_batch_set_lockstep.restype = ip
+    lib.rfnse_batch_lockstep.argtypes = [vp]
+    lib.rfnse_batch_lockstep.restype = ip
     lib.rfnse_test_fail_allocations.argtypes = [ctypes.c_longlong]
     lib.rfnse_test_fail_allocations.restype = ip
     if path == _build.library_path():
@@ -467,6 +472,14 @@ class Batch:
 
     def tuned_launches(self) -> int:
         return sum(int(self.lib.rfnse_tuned_launches(c)) for c in self.ctx)
+
+    def set_lockstep(self, on: bool):
+        """Lock-step mode (one launch per pass and kernel for all instances) on or off."""
+        self._check(self.lib.rfnse_batch_set_lockstep(self.h, int(on)))
+
+    @property
+    def lockstep(self) -> bool:
+        return bool(self.lib.rfnse_batch_lockstep(self.h))
 
     def run(self, nsteps: int, allow_noconv: bool = False):
         """Advance every instance nsteps; returns (iters, relres) of shape (nsteps, count)."""
