@@ -145,6 +145,9 @@ def parse():
                     help="only time the cooperative Arnoldi kernel (MGS + Givens) per column j on the 2-D and "
                          "3-D grid sizes and print the times")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch geometry of the line passes")
+    ap.add_argument("--arnoldi-grid", type=int, default=0,
+                    help="force the Arnoldi kernel's launch after tuning (rfnse_set_arnoldi_grid: > 0 blocks of "
+                         "the grid-wide kernel, -8 / -16 one cluster of that many CTAs; 0 = as tuned)")
     ap.add_argument("--no-lockstep", action="store_true",
                     help="batches run one CUDA graph branch per instance instead of the lock-step launches")
     ap.add_argument("--no-3d", action="store_true",
@@ -478,7 +481,11 @@ def measure(args, env: Env, name: str, instances: int, steps: int, warmup: int, 
                 b.set_lockstep(False)
             if not args.no_autotune:
                 nc, ch = b.autotune(reps=5)
-                tuning.setdefault(precision, {"configs": nc, "changed": ch})
+                tuning.setdefault(precision, {"configs": nc, "changed": ch,
+                                              "arnoldi_grid": int(b.lib.rfnse_arnoldi_grid(b.ctx[0]))})
+            if args.arnoldi_grid:
+                for cx in b.ctx:
+                    b._check(b.lib.rfnse_set_arnoldi_grid(cx, args.arnoldi_grid), cx)
             for i, (p, u0) in enumerate(inst):
                 b.set_state(i, torch.from_numpy(u0.ravel().copy()).to(dev))
             torch.cuda.synchronize()
@@ -489,7 +496,10 @@ def measure(args, env: Env, name: str, instances: int, steps: int, warmup: int, 
             s = rfnse.Solver(p, precision=precision, stream=st, device_loop=device_loop)
             if not args.no_autotune:
                 nc, ch, sp = s.autotune(reps=5)
-                tuning.setdefault(precision, {"configs": nc, "changed": ch, "est_speedup": sp})
+                tuning.setdefault(precision, {"configs": nc, "changed": ch, "est_speedup": sp,
+                                              "arnoldi_grid": int(s.lib.rfnse_arnoldi_grid(s.h))})
+            if args.arnoldi_grid:
+                s._check(s.lib.rfnse_set_arnoldi_grid(s.h, args.arnoldi_grid))
             s.set_state(torch.from_numpy(u0.ravel().copy()).to(dev))
             solvers.append(s)
         torch.cuda.synchronize()
@@ -592,7 +602,9 @@ def measure(args, env: Env, name: str, instances: int, steps: int, warmup: int, 
     if clk:
         out["clocks"] = clk
     out["autotune"] = ({"mixed": tuning.get(1), "what": "rfnse_autotune: lines per block, FFT threads per line "
-                        "and kernel variant of every line-pass configuration, chosen by timing (set-up, not timed)"}
+                        "and kernel variant of every line-pass configuration, and the Arnoldi kernel's launch "
+                        "(arnoldi_grid: > 0 blocks of the grid-wide kernel, < 0 one cluster of that many CTAs), "
+                        "chosen by timing (set-up, not timed)"}
                        if not args.no_autotune else None)
 
     # the largest kernel classes, each timed launch by launch in a further serial run of the same steps

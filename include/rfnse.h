@@ -285,21 +285,36 @@ int rfnse_apply_prec_static(const rfnse_params* p, const void* v, void* z, const
    lines adjacent in x), the threads per line of the FFT (runtime-length FFT: one or two radix-4
    butterflies per thread; fixed-length FP32 FFT: L/8 threads, radix-8 butterflies) and the kernel
    variant (fixed-length FP32 passes: operands prefetched into registers or staged through shared
-   memory).  Each pass configuration runs once with its real operands (the context's work vectors,
+   memory), and the grid of the cooperative Arnoldi kernel (one to four blocks per SM, all co-resident;
+   for N > 4096).  Each pass configuration runs once with its real operands (the context's work vectors,
    which it overwrites; the time-stepping state is untouched), then every candidate geometry is timed
    with CUDA events over `reps` launches (1..1000) on the context's stream and the fastest is kept in
    the context; later launches of that configuration use it, and the context's cached solve graphs are
    dropped so that the next solve captures them again.  Choices are shared between contexts of the same
    grid on the same device unless force = 1.  The arithmetic of a line does not depend on the
    geometry; only the order of the first MGS dot product's block partials does, so results agree with
-   an untuned context to rounding.  n_configs, n_changed (host, may be NULL): configurations tuned and
+   an untuned context to rounding (the Arnoldi kernel's grid changes the order of its partial sums).
+   n_configs, n_changed (host, may be NULL): configurations tuned (passes, plus the Arnoldi grid) and
    how many got a geometry other than the default; est_speedup (host, may be NULL): summed default over
-   summed chosen duration, one launch of each configuration.  Synchronises the stream.
+   summed chosen duration, one launch of each pass configuration.  Synchronises the stream.
    Errors: EINVAL, ECUDA. */
 int rfnse_autotune(rfnse_ctx* ctx, int reps, int force, int* n_configs, int* n_changed, double* est_speedup);
 
 /* Number of line-pass launches of ctx whose geometry came from rfnse_autotune's choices. */
 long long rfnse_tuned_launches(const rfnse_ctx* ctx);
+
+/* The launch of the Arnoldi kernel (modified Gram-Schmidt, Givens, convergence test; the paper's
+   PGMRES orthogonalisation) used by ctx's solves: blocks > 0 runs the cooperative grid-wide kernel on
+   that many blocks (all co-resident, a bounded grid-wide barrier after each sweep; 1 for N <= 4096);
+   blocks = -8 or -16 runs it on one thread-block cluster of that many CTAs (hardware cluster barriers,
+   reductions through distributed shared memory; for small grids, whose sweeps cost less than a
+   grid-wide barrier); 0 restores the default.  rfnse_autotune sets it by timing.  The arithmetic is
+   the same; only the order of the partial sums differs.  Errors: EINVAL (a grid that cannot be
+   resident on this device). */
+int rfnse_set_arnoldi_grid(rfnse_ctx* ctx, int blocks);
+
+/* The current launch of ctx's Arnoldi kernel (as rfnse_set_arnoldi_grid takes it). */
+int rfnse_arnoldi_grid(const rfnse_ctx* ctx);
 
 /* ---- instrumentation -------------------------------------------------------------------------- */
 

@@ -295,7 +295,7 @@ int rfnse_create(const rfnse_params* p, void* stream, rfnse_ctx** out) {
   if (c->debug) chk(dalloc(&c->dbg_count, 1));
   c->coop_blocks = coop_blocks_for(N);
   chk(dalloc(&c->bar, 1));
-  chk(dalloc(&c->coop_partials, 2 * (size_t)c->coop_blocks));
+  chk(dalloc(&c->coop_partials, 2 * (size_t)coop_blocks_max(N)));  // room for any grid the tuner picks
   chk(dalloc(&c->dot_part, (size_t)kDot0MaxBlocks));
   chk(dalloc(&c->nrm_part, 3 * (size_t)kNormPartMax));
   if (e == cudaSuccess) chk(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
@@ -498,6 +498,31 @@ int rfnse_autotune(rfnse_ctx* c, int reps, int force, int* n_configs, int* n_cha
 }
 
 long long rfnse_tuned_launches(const rfnse_ctx* c) { return c ? c->tuned_launches : 0; }
+
+int rfnse_set_arnoldi_grid(rfnse_ctx* c, int blocks) {
+  if (!c) return RFNSE_EINVAL;
+  int g = blocks;
+  if (g == 0) g = coop_blocks_for(c->N);
+  else if (g > 0 && (c->N <= 4096 ? g != 1 : g > coop_blocks_max(c->N))) g = 0;
+  else if (g < 0 && (g != -8 && g != -16)) g = 0;
+  else if (g < 0 && !mgs_cluster_fits(-g)) g = 0;
+  if (g == 0) {
+    c->err = "rfnse_set_arnoldi_grid: blocks must be 1..co-resident maximum, -8 or -16 (a cluster that fits)";
+    return RFNSE_EINVAL;
+  }
+  RFNSE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->coop_blocks = g;
+  for (int a = 0; a < 2; ++a)  // the cached solve graphs hold the old launch: capture them again
+    for (int h = 0; h < 2; ++h) {
+      if (c->graph_exec[a][h]) cudaGraphExecDestroy(c->graph_exec[a][h]);
+      if (c->graph[a][h]) cudaGraphDestroy(c->graph[a][h]);
+      c->graph_exec[a][h] = nullptr;
+      c->graph[a][h] = nullptr;
+    }
+  return RFNSE_OK;
+}
+
+int rfnse_arnoldi_grid(const rfnse_ctx* c) { return c ? c->coop_blocks : 0; }
 
 int rfnse_test_fail_allocations(long long after) {
   g_alloc_budget.store(after < 0 ? -1 : after);

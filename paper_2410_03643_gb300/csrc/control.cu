@@ -3,11 +3,15 @@
 // kernels that start a solve or a cycle and decide, on the device, whether the next Arnoldi step,
 // restart or refinement cycle runs.  With a CUDA graph whose conditional WHILE nodes read the
 // handles these kernels set, a whole solve runs without the host.
+#include <cooperative_groups.h>
 #include <cmath>
 #include "internal.cuh"
 #include "coop.cuh"
 
 namespace rfnse {
+
+__device__ __forceinline__ void givens_finish(GmresState* gs, int j, double nrm2, double2* w, const SolveCfg& cfg,
+                                              cudaGraphConditionalHandle h_inner, int set_cond);
 
 // Arnoldi step j = gs->j: w holds A M^{-1} v_j.  Modified Gram-Schmidt (for i = 0..j:
 // h_ij = <v_i, w>, w -= h_ij v_i; one pass per i fusing the previous subtraction with the next dot),
@@ -72,6 +76,14 @@ __global__ void __launch_bounds__(kCtlThreads) k_mgs_step(GmresState* gs, const 
     }
   }
   if (threadIdx.x != 0) return;  // one block is left: the last to arrive (or the only one)
+  givens_finish(gs, j, nrm2, w, cfg, h_inner, set_cond);
+}
+
+// The end of Arnoldi step j (one thread): h_{j+1,j} = sqrt(nrm2), the previous rotations on column j,
+// the new rotation, g, the convergence test, the state for the next column and, if set_cond, the
+// inner-loop condition.
+__device__ __forceinline__ void givens_finish(GmresState* gs, int j, double nrm2, double2* w, const SolveCfg& cfg,
+                                              cudaGraphConditionalHandle h_inner, int set_cond) {
   double* Hc = gs->H + (size_t)j * (kMaxM + 1);
   const double hnext = sqrt(nrm2);
   Hc[j + 1] = hnext;
@@ -103,6 +115,59 @@ __global__ void __launch_bounds__(kCtlThreads) k_mgs_step(GmresState* gs, const 
   const int stop = done != 0 || gs->it >= cfg.max_it || gs->err;
   gs->no_restart = stop;
   if (set_cond) cudaGraphSetConditional(h_inner, (!stop && j + 1 < cfg.m) ? 1u : 0u);
+}
+
+// The same Arnoldi step on one thread-block cluster of CL CTAs (small grids: a sweep moves a few MB
+// from L2, and the grid-wide barrier of k_mgs_step, global atomics and polling, costs more than the
+// sweep).  Each CTA leaves its partial of a sweep in its own shared memory; after the cluster barrier
+// (hardware, no polling) every CTA reads the CL partials through distributed shared memory in rank
+// order, so all hold the same sum.  The other SMs stay free for concurrent work.
+constexpr int kClThreads = 1024;
+__global__ void __launch_bounds__(kClThreads) k_mgs_cluster(GmresState* gs, const double2* __restrict__ V,
+                                                            long long ldv, double2* __restrict__ w, long long N,
+                                                            SolveCfg cfg, cudaGraphConditionalHandle h_inner,
+                                                            int set_cond, const double* __restrict__ pre_part,
+                                                            int pre_n) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int nr = (int)cl.num_blocks();
+  __shared__ double sh[32];
+  __shared__ double part[2];  // this CTA's partial of the current sweep (by sweep parity)
+  __shared__ double bc;
+  const int j = gs->j;
+  double hprev = 0.0, nrm2 = 0.0;
+  int i0 = 0;
+  if (pre_n > 0) {
+    hprev = fixed_sum(pre_part, pre_n, sh);
+    if (rank == 0 && threadIdx.x == 0) gs->H[(size_t)j * (kMaxM + 1)] = hprev;
+    i0 = 1;
+  }
+  for (int i = i0; i <= j + 1; ++i) {
+    const double2* vi = (i <= j) ? V + (size_t)i * ldv : nullptr;
+    const double2* vp = (i > 0) ? V + (size_t)(i - 1) * ldv : nullptr;
+    double acc = mgs_sweep(w, vi, vp, hprev, N, (long long)rank * blockDim.x + threadIdx.x,
+                           (long long)nr * blockDim.x);
+    acc = block_sum_c(acc, sh);
+    if (threadIdx.x == 0) part[i & 1] = acc;
+    cl.sync();  // the partials of sweep i are complete (and w's updates visible in the cluster)
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int r = 0; r < nr; ++r) t += *cl.map_shared_rank(&part[i & 1], r);
+      bc = t;
+    }
+    __syncthreads();
+    const double sum = bc;
+    __syncthreads();
+    if (i <= j) {
+      hprev = sum;
+      if (rank == 0 && threadIdx.x == 0) gs->H[(size_t)j * (kMaxM + 1) + i] = sum;
+    } else {
+      nrm2 = sum;
+    }
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+  if (rank == 0 && threadIdx.x == 0) givens_finish(gs, j, nrm2, w, cfg, h_inner, set_cond);
 }
 
 // ||x|| into gs (beta, 1/beta, g = beta e_1), fixed-order reduction; then, by mode:
@@ -370,6 +435,34 @@ static inline unsigned ew_blocks_c(long long N) {
   return (unsigned)b;
 }
 
+int coop_blocks_max(long long N) {
+  if (N <= 4096) return 1;
+  int dev = 0, sms = 152, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mgs_step, kCtlThreads, 0);
+  if (per_sm > 4) per_sm = 4;
+  long long b = (long long)sms * (per_sm < 1 ? 1 : per_sm);
+  const long long need = (N + kCtlThreads - 1) / kCtlThreads;
+  if (b > need) b = need;
+  return (int)(b < 1 ? 1 : b);
+}
+
+// A column of the GMRES state for timing the Arnoldi kernel (rfnse_autotune): j, no convergence test
+// that stops (ref 1, tol 0), counters cleared.
+__global__ void k_set_column(GmresState* gs, int j) {
+  gs->j = j;
+  gs->done = 0;
+  gs->it = 0;
+  gs->err = 0;
+  gs->ref = 1.0;
+  gs->tol = 0.0;
+}
+void launch_set_column(GmresState* gs, int j, cudaStream_t s) {
+  count_launch();
+  k_set_column<<<1, 1, 0, s>>>(gs, j);
+}
+
 int coop_blocks_for(long long N) {
   int dev = 0, sms = 152, per_sm = 1;
   cudaGetDevice(&dev);
@@ -387,10 +480,56 @@ int coop_blocks_for(long long N) {
   return (int)b;
 }
 
+// blocks < 0: one cluster of -blocks CTAs (k_mgs_cluster)
+static cudaError_t launch_mgs_cluster(GmresState* gs, const double2* V, long long ldv, double2* w, long long N,
+                                      const SolveCfg& cfg, cudaGraphConditionalHandle h_inner, int set_cond,
+                                      int csize, cudaStream_t s, const double* pre_part, int pre_n) {
+  static const cudaError_t attr = cudaFuncSetAttribute(k_mgs_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (attr != cudaSuccess) return attr;
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)csize);
+  lc.blockDim = dim3(kClThreads);
+  lc.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)csize;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  count_launch();
+  return cudaLaunchKernelEx(&lc, k_mgs_cluster, gs, V, ldv, w, N, cfg, h_inner, set_cond, pre_part, pre_n);
+}
+
+// Whether one cluster of csize CTAs of the cluster Arnoldi kernel can be resident on this device.
+bool mgs_cluster_fits(int csize) {
+  if (cudaFuncSetAttribute(k_mgs_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)csize);
+  lc.blockDim = dim3(kClThreads);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)csize;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, k_mgs_cluster, &lc) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return nclusters >= 1;
+}
+
 cudaError_t launch_mgs_step(GmresState* gs, const double2* V, long long ldv, double2* w, long long N,
                             double* partials, GridBarrier* bar, const SolveCfg& cfg,
                             cudaGraphConditionalHandle h_inner, int set_cond, int blocks, cudaStream_t s,
                             const double* pre_part, int pre_n) {
+  if (blocks < 0) return launch_mgs_cluster(gs, V, ldv, w, N, cfg, h_inner, set_cond, -blocks, s, pre_part, pre_n);
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3((unsigned)blocks);
   lc.blockDim = dim3(kCtlThreads);

@@ -131,7 +131,12 @@ struct GridBarrier {
 
 // ---- device-side control (control.cu) -----------------------------------------------------------
 int coop_blocks_for(long long N);  // blocks of the cooperative Arnoldi kernel (all co-resident)
-// pre_part / pre_n: partials of h_0j = <v_0, w> written by the last product pass (pre_n = 0: none)
+int coop_blocks_max(long long N);  // the most it may use (up to four per SM, co-resident)
+bool mgs_cluster_fits(int csize);  // one cluster of csize CTAs of the cluster variant is resident
+void launch_set_column(GmresState* gs, int j, cudaStream_t s);  // state for timing column j (autotune)
+// pre_part / pre_n: partials of h_0j = <v_0, w> written by the last product pass (pre_n = 0: none);
+// blocks > 0: the cooperative grid-wide kernel on that many blocks; blocks < 0: one thread-block cluster
+// of -blocks CTAs (hardware cluster barriers, distributed-shared-memory reductions)
 cudaError_t launch_mgs_step(GmresState* gs, const double2* V, long long ldv, double2* w, long long N,
                             double* partials, GridBarrier* bar, const SolveCfg& cfg,
                             cudaGraphConditionalHandle h_inner, int set_cond, int blocks, cudaStream_t s,
@@ -293,7 +298,7 @@ struct rfnse_ctx {
   // device-side control: cooperative Arnoldi kernel and one CUDA graph per (precision, half)
   rfnse::GridBarrier* bar = nullptr;
   double* coop_partials = nullptr;   // 2 * coop_blocks
-  int coop_blocks = 1;
+  int coop_blocks = 1;               // < 0: one cluster of -coop_blocks CTAs (chosen by rfnse_autotune)
   double* dot_part = nullptr;        // kDot0MaxBlocks partials of <v_0, w> from the last product pass
   int dot0_blocks = 0;               // how many the last such launch wrote (0: none)
   // block partials of squared norms left by the kernel that produced the vector, so that the solve's

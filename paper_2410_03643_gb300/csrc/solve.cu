@@ -782,6 +782,68 @@ rfnse_status autotune(rfnse_ctx* c, int reps, int force, int* n_configs, int* n_
     t_best += tb;
     t_dflt += td;
   }
+  // the cooperative Arnoldi kernel's grid: 1..4 blocks per SM (all co-resident), timed on column j = 1
+  // of the context's own basis (two sweeps and a grid-wide barrier, then the norm sweep)
+  const bool tune_mgs = st == RFNSE_OK && c->N > 4096 && c->p.restart >= 1;
+  if (tune_mgs) {
+    const TuneMemoKey mk{dev, -1, (int)(c->N >> 31), (int)(c->N & 0x7fffffff), 0, 0ull};
+    int best = -1;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      const auto it = g_tune_memo.find(mk);
+      if (!force && it != g_tune_memo.end()) best = it->second.first.B;
+    }
+    if (best < 0) {
+      const int bmax = coop_blocks_max(c->N);
+      int sms = 152;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      const SolveCfg cfg = make_cfg(c, c->p.precision == 1 ? 1 : 0);
+      double tbest = std::numeric_limits<double>::infinity();
+      // candidates: 1..4 blocks per SM of the grid-wide kernel; for grids of at most 2^21 points also
+      // one cluster of 8 or 16 CTAs (negative counts)
+      std::vector<int> cands;
+      for (int k = 1; k <= 4; ++k) {
+        const int blocks = std::min(bmax, sms * k);
+        if (k > 1 && blocks == std::min(bmax, sms * (k - 1))) break;
+        cands.push_back(blocks);
+      }
+      if (c->N <= (1LL << 21))
+        for (int cs : {8, 16})
+          if (mgs_cluster_fits(cs)) cands.push_back(-cs);
+      for (const int blocks : cands) {
+        auto one = [&]() {
+          launch_set_column(c->gs, 1, c->stream);
+          return launch_mgs_step(c->gs, c->V, c->N, c->w, c->N, c->coop_partials, c->bar, cfg, 0, 0, blocks,
+                                 c->stream);
+        };
+        cudaError_t e = one();
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = one();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          continue;
+        }
+        if (ms < tbest) {
+          tbest = ms;
+          best = blocks;
+        }
+      }
+      if (best > 0) {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_memo[mk] = {PassGeom{best, 0, 0}, PassGeom{c->coop_blocks, 0, 0}};
+      }
+    }
+    if (best > 0) {
+      if (best != c->coop_blocks) ++changed;
+      c->coop_blocks = best;
+    }
+    RFNSE_CUDA_TRY(c, cudaMemsetAsync(c->gs, 0, sizeof(GmresState), c->stream));
+    RFNSE_CUDA_TRY(c, cudaMemsetAsync(c->bar, 0, sizeof(GridBarrier), c->stream));
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != RFNSE_OK) {
@@ -796,7 +858,7 @@ rfnse_status autotune(rfnse_ctx* c, int reps, int force, int* n_configs, int* n_
       c->graph_exec[a][h] = nullptr;
       c->graph[a][h] = nullptr;
     }
-  if (n_configs) *n_configs = (int)rec.size();
+  if (n_configs) *n_configs = (int)rec.size() + (tune_mgs ? 1 : 0);
   if (n_changed) *n_changed = changed;
   if (est_speedup) *est_speedup = (t_best > 0.0) ? t_dflt / t_best : 1.0;
   return RFNSE_OK;

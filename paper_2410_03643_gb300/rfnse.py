@@ -59,7 +59,7 @@ EXPORTED = ("rfnse_default_params", "rfnse_create", "rfnse_destroy", "rfnse_last
             "rfnse_tape_forward", "rfnse_tape_backward", "rfnse_adjoint_solve", "rfnse_tban_solve",
             "rfnse_selftest_bounded_wait", "rfnse_test_fail_allocations", "rfnse_apply_prec_static",
             "rfnse_autotune", "rfnse_tuned_launches", "rfnse_batch_autotune", "rfnse_batch_set_lockstep",
-            "rfnse_batch_lockstep")
+            "rfnse_batch_lockstep", "rfnse_set_arnoldi_grid", "rfnse_arnoldi_grid")
 
 K_INSCALE, K_DST, K_LAM, K_DSCALE, K_TOEP_X, K_TOEP_ACC, K_FP32, K_DF, K_ARNOLDI = 1, 2, 4, 8, 16, 32, 256, 1024, 2048
 
@@ -140,6 +140,10 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     lib.rfnse_tuned_launches.restype = ctypes.c_longlong
     lib.rfnse_batch_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.rfnse_batch_autotune.restype = ip
+    lib.rfnse_set_arnoldi_grid.argtypes = [vp, ip]
+    lib.rfnse_set_arnoldi_grid.restype = ip
+    lib.rfnse_arnoldi_grid.argtypes = [vp]
+    lib.rfnse_arnoldi_grid.restype = ip
     lib.rfnse_batch_set_lockstep.argtypes = [vp, ip]
     lib.rfnse_batch_set_lockstep.restype = ip
     lib.rfnse_batch_lockstep.argtypes = [vp]
