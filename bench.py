@@ -96,13 +96,26 @@ PROFILED = {
     "1d": ("arnoldi", "fp32_all_1d", "df_toep_x"),
 }
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch (ncu, one capture each) of a class on a
-# workload, with the digest of the class's sources when it was taken: once a source has changed the
-# figure no longer describes the kernel and the line reports traffic null.
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of a class on a workload: the mean over the
+# launches of the class captured by ncu in `bench.py --kernel-case 2d|3d` (one mixed solve of the
+# workload's grid, the same kernels and vector sizes), with the digest of the class's sources when the
+# capture was taken: once a source has changed the figure no longer describes the kernel and the line
+# reports traffic null.
 TRAFFIC = {
-    ("2d", "arnoldi"): (11744538, "dfc6e2f299f1"),
-    ("2d", "fp32_fused_x"): (5288960, "aa1b09e3a567"),
-    ("2d", "df_toep_x"): (6360320, "344a18e48fe5"),
+    ("2d", "arnoldi"): (10489536, "6bffcb343161"),
+    ("2d", "fp32_fused_x"): (5288576, "cab47e75cad9"),
+    ("2d", "fp32_dst"): (4217003, "cab47e75cad9"),
+    ("2d", "fp32_dst_lam"): (4217472, "cab47e75cad9"),
+    ("2d", "fp32_toep_acc"): (8414592, "cab47e75cad9"),
+    ("2d", "df_toep_x"): (6360576, "19ad2bc4295e"),
+    ("2d", "df_toep_acc"): (8449536, "19ad2bc4295e"),
+    ("3d", "arnoldi"): (1811794602, "6bffcb343161"),
+    ("3d", "fp32_fused_x"): (557157376, "cab47e75cad9"),
+    ("3d", "fp32_dst"): (350335744, "cab47e75cad9"),
+    ("3d", "fp32_dst_lam"): (371992064, "cab47e75cad9"),
+    ("3d", "fp32_toep_acc"): (424224640, "cab47e75cad9"),
+    ("3d", "df_toep_x"): (880631808, "19ad2bc4295e"),
+    ("3d", "df_toep_acc"): (756285952, "19ad2bc4295e"),
 }
 
 
