@@ -102,7 +102,11 @@ long long rfnse_size(const rfnse_ctx* ctx);
 /* Load the time-stepping state.  step = 0: u_cur = u^0 (initial data on the grid, Sec. 2.1) and
    u_prev is ignored (may be NULL).  step >= 1: (u_prev, u_cur) = (u^{step-1}, u^{step}), e.g. to
    resume from rfnse_get_state.  on_device = 1: device pointers; 0: host pointers.  Each holds N
-   complex FP64 values.  Errors: EINVAL, ECUDA. */
+   complex FP64 values.  When the context has taken a step and step >= 1, the loaded vectors are
+   compared bit by bit with the context's own (u^{n-1}, u^n): each one that comes back unchanged (a
+   caller continuing its own run through host buffers) keeps what the context had computed for it
+   (the mixed form's cached T u), so the next step costs no more than without the reload; the values
+   used are the loaded ones in every case.  Synchronises the stream.  Errors: EINVAL, ECUDA. */
 int rfnse_set_state(rfnse_ctx* ctx, const void* u_prev, const void* u_cur, int step, int on_device);
 
 /* Read the state (u^{step-1}, u^{step}) and step.  u_prev is not written when step == 0.  Either

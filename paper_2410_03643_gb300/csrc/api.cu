@@ -117,6 +117,7 @@ void free_ctx(rfnse_ctx* c) {
   cudaFree(c->partials);
   cudaFree(c->counter);
   cudaFree(c->dbg_count);
+  cudaFree(c->cmp_flag);
   cudaFree(c->gs);
   if (c->peek) cudaFreeHost(c->peek);
   for (cudaEvent_t ev : c->prof_events) cudaEventDestroy(ev);
@@ -293,6 +294,7 @@ int rfnse_create(const rfnse_params* p, void* stream, rfnse_ctx** out) {
   }
   c->use_graphs = p->device_loop != 0 && !c->debug;  // debug checks synchronise after every pass
   if (c->debug) chk(dalloc(&c->dbg_count, 1));
+  chk(dalloc(&c->cmp_flag, 2));
   c->coop_blocks = coop_blocks_for(N);
   chk(dalloc(&c->bar, 1));
   chk(dalloc(&c->coop_partials, 2 * (size_t)coop_blocks_max(N)));  // room for any grid the tuner picks
@@ -371,6 +373,35 @@ int rfnse_set_state(rfnse_ctx* c, const void* u_prev, const void* u_cur, int ste
   }
   const size_t bytes = sizeof(double2) * (size_t)c->N;
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  // A caller that continues its own run through host buffers loads the state the last step left
+  // (u^{n-1}, u^n): the history slots whose contents come back unchanged keep their cached T u (mixed
+  // form), so the next right-hand side needs no Toeplitz product.  The uploads land in the free slot
+  // and a work vector and are compared bit by bit with the slots on the device.
+  const int p = c->iprev, q = c->icur, f = 3 - p - q;
+  if (step > 0 && c->step > 0 && c->cmp_flag && (c->tu_valid[p] || c->tu_valid[q])) {
+    RFNSE_CUDA_TRY(c, cudaMemcpyAsync(c->u[f], u_prev, bytes, kind, c->stream));
+    RFNSE_CUDA_TRY(c, cudaMemcpyAsync(c->t2, u_cur, bytes, kind, c->stream));
+    launch_differs(c->u[f], c->u[p], c->N, c->cmp_flag, c->stream);
+    launch_differs(c->t2, c->u[q], c->N, c->cmp_flag + 1, c->stream);
+    int differs[2] = {1, 1};
+    RFNSE_CUDA_TRY(c, cudaMemcpyAsync(differs, c->cmp_flag, sizeof(differs), cudaMemcpyDeviceToHost, c->stream));
+    RFNSE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const int np = differs[0] ? f : p;  // u^{n-1}: the uploaded copy, or the identical slot
+    int nq = q;                         // u^n: the identical slot, or the uploaded copy moved into a slot
+    if (differs[1]) {                   // other than u^{n-1}'s
+      nq = (np == f) ? q : f;
+      RFNSE_CUDA_TRY(c, cudaMemcpyAsync(c->u[nq], c->t2, bytes, cudaMemcpyDeviceToDevice, c->stream));
+      RFNSE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    const bool keep_p = !differs[0] && c->tu_valid[p], keep_q = !differs[1] && c->tu_valid[q];
+    for (int i = 0; i < 3; ++i) c->tu_valid[i] = false;
+    c->tu_valid[np] = keep_p;  // keep_p implies np == p, keep_q implies nq == q
+    c->tu_valid[nq] = keep_q;
+    c->iprev = np;
+    c->icur = nq;
+    c->step = step;
+    return RFNSE_OK;
+  }
   c->iprev = 0;
   c->icur = 1;
   for (int i = 0; i < 3; ++i) c->tu_valid[i] = false;

@@ -188,6 +188,8 @@ void launch_combine_f32_add(const float2* Z, long long ldz, const GmresState* gs
 void launch_diag(const double2* u, const double2* u2, double* D, double rho_dt, long long N, cudaStream_t s);
 void launch_neg_i(const double2* b, double2* f, long long N, cudaStream_t s);
 void launch_zero(double2* x, long long N, cudaStream_t s);
+// *flag = 1 if a and b differ in any bit of their N complex FP64 values, else 0
+void launch_differs(const double2* a, const double2* b, long long N, int* flag, cudaStream_t s);
 void launch_start_cycle(GmresState* gs, double ref, double tol, cudaStream_t s);
 // Tu = scale (D x - i (f - x - r)) from the residual r = f - x - i(T - D)x
 void launch_tu_from_residual(const double* D, const double2* f, const double2* x, const double2* r, double2* Tu,
@@ -334,6 +336,7 @@ struct rfnse_ctx {
   bool debug = false;
   int* dbg_count = nullptr;        // device: non-finite values found by the last scan
   std::string dbg_first;           // the first pass whose output had a non-finite value ("" if none)
+  int* cmp_flag = nullptr;         // device: result of the bitwise comparison in rfnse_set_state
   // kernel-class profiling (rfnse_profile): CUDA events around every launch of one pass kind
   int prof_kind = 0;
   std::vector<cudaEvent_t> prof_events;  // pairs (start, stop)

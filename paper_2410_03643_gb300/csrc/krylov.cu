@@ -311,4 +311,19 @@ void launch_step_prep(rfnse_ctx* c, const double2* uc, const double2* up, const 
 }
 void launch_zero(double2* x, long long N, cudaStream_t s) { k_zero<<<ew_blocks(N), 256, 0, s>>>(x, N); }
 
+__global__ void k_differs(const double2* __restrict__ a, const double2* __restrict__ b, long long N, int* flag) {
+  int d = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double2 u = a[i], v = b[i];
+    d |= (__double_as_longlong(u.x) != __double_as_longlong(v.x)) | (__double_as_longlong(u.y) != __double_as_longlong(v.y));
+  }
+  if (__syncthreads_or(d) && threadIdx.x == 0) atomicExch(flag, 1);
+}
+__global__ void k_clear_flag(int* flag) { *flag = 0; }
+void launch_differs(const double2* a, const double2* b, long long N, int* flag, cudaStream_t s) {
+  count_launch(2);
+  k_clear_flag<<<1, 1, 0, s>>>(flag);
+  k_differs<<<ew_blocks(N), 256, 0, s>>>(a, b, N, flag);
+}
+
 }  // namespace rfnse

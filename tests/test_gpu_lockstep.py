@@ -77,8 +77,9 @@ def test_lockstep_with_one_instance_and_with_uneven_sizes():
 
 
 def test_lockstep_reload_mid_run_and_switch_modes():
-    """Reloading one instance mid-run sends the batch back to per-instance first steps and then into
-    the lock-step graph again; switching the mode between steps keeps every trajectory."""
+    """Reloading an instance with its own state keeps its cached products (the batch stays in
+    lock-step); reloading it with new contents sends the batch back to per-instance first steps and
+    then into the lock-step graph again; switching the mode between steps keeps every trajectory."""
     from paper_2410_03643_gb300 import Batch
     inst = _instances(seed=21, count=3)
     b = Batch([p for p, _ in inst], precision=1)
@@ -88,7 +89,11 @@ def test_lockstep_reload_mid_run_and_switch_modes():
     b.run(3)
     up, uc, step = b.get_state(1)
     b.set_state(1, uc, up, step)
-    b.run(2)
+    b.run(1)
+    p1, u01 = inst[1]
+    ref1, _, _ = SchemeOracle(p1).run(u01, 4)
+    b.set_state(1, dev(ref1[3]), dev(ref1[2]), 4)
+    b.run(1)
     assert b.lib.rfnse_batch_set_lockstep(b.h, 0) == 0
     b.run(1)
     assert b.lib.rfnse_batch_set_lockstep(b.h, 1) == 0

@@ -215,6 +215,45 @@ def test_restart_and_resume_state():
     assert rel(host(uc2, p.shape), ref[3]) < 1e-10
 
 
+def test_host_continuation_keeps_cached_products():
+    """A run continued step by step through host buffers (get the state, load it back, take one step:
+    what the end-to-end bench does) keeps the mixed form's cached T u, so it reproduces the continuous
+    run bit for bit; a reload that changes u^{n-1} or u^n makes the context use the loaded values."""
+    p = W.Problem(d=2, n=(127, 63), lo=(-8.0, -6.0), hi=(8.0, 6.0), alpha=1.6, rho=2.0, dt=0.01, tol=1e-10)
+    u0 = W.u0_sech_product(p, [1.0, -0.5])
+    nsteps = 6
+    a = Solver(p, precision=1)
+    a.set_state(dev(u0))
+    traj = torch.empty(nsteps * p.size, dtype=torch.complex128, device="cuda")
+    a.run(nsteps, traj)
+    want = traj.cpu().numpy().reshape((nsteps,) + p.shape)
+    a.close()
+    b = Solver(p, precision=1)
+    b.set_state(dev(u0))
+    b.run(2)
+    out = np.empty(p.size, dtype=np.complex128)
+    for k in range(2, nsteps):
+        up, uc, step = b.get_state()
+        assert step == k
+        b.set_state_host(uc.cpu().numpy(), up.cpu().numpy(), step)
+        b.run_host(1, out)
+        assert np.array_equal(out.reshape(p.shape), want[k]), k
+    # a changed u^n (and, separately, u^{n-1}) is taken as loaded
+    o = SchemeOracle(p)
+    for which in (0, 1):
+        up, uc, step = b.get_state()
+        up_h, uc_h = up.cpu().numpy(), uc.cpu().numpy()
+        if which == 0:
+            uc_h = uc_h * (1.0 + 1e-3)
+        else:
+            up_h = up_h * (1.0 - 1e-3)
+        b.set_state_host(uc_h, up_h, step)
+        b.run_host(1, out)
+        ref, _, _ = o.step(up_h.reshape(p.shape), uc_h.reshape(p.shape))
+        assert rel(out.reshape(p.shape), ref) < 1e-9, which
+    b.close()
+
+
 def test_alpha2_rho0_single_iteration():
     p = SMALL[2].replace(alpha=2.0, rho=0.0, tol=1e-10)
     s = Solver(p)
