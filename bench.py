@@ -76,7 +76,7 @@ _PASS_SRC = ("passes.cuh", "fft_fixed.cuh", "fft_line.cuh", "cplx.cuh")
 _DF_SRC = ("toep_df.cu", "dfloat.cuh", "fft_fixed.cuh", "cplx.cuh")
 KERNEL_CLASSES = {
     "arnoldi": (2048, "alu", "k_mgs_step (cooperative MGS + Givens + convergence test, one launch per Arnoldi "
-                             "step)", ("control.cu",)),
+                             "step)", ("control.cu", "coop.cuh")),
     "fp32_fused_x": (256 | 2 | 8 | 16, "hbm", "line pass <float, F_DST|F_DSCALE|F_TOEP_X> (inverse DST x + "
                                               "(wI+D) sub-solve + Toeplitz x)", _PASS_SRC),
     "fp32_dst": (256 | 2, "hbm", "line pass <float, F_DST> (DST x with the Arnoldi scaling folded in; DST y in 3-D)",

@@ -10,111 +10,52 @@
 
 namespace rfnse {
 
-__device__ __forceinline__ void givens_finish(GmresState* gs, int j, double nrm2, double2* w, const SolveCfg& cfg,
-                                              cudaGraphConditionalHandle h_inner, int set_cond);
-
 // Arnoldi step j = gs->j: w holds A M^{-1} v_j.  Modified Gram-Schmidt (for i = 0..j:
-// h_ij = <v_i, w>, w -= h_ij v_i; one pass per i fusing the previous subtraction with the next dot),
+// h_ij = <v_i, w>, w -= h_ij v_i; one sweep per i fusing the previous subtraction with the next dot),
 // h_{j+1,j} = ||w||, the Givens update of column j and the convergence test; then the state for the
 // next column (src = w, scale = 1/h_{j+1,j}, j + 1) and, if set_cond, the inner-loop condition.
 // With pre_n > 0 the product pass that wrote w has also left pre_n block partials of h_0j = <v_0, w>:
-// every block sums them in a fixed order and the first pass (and its grid-wide reduction) is skipped.
+// every block sums them in a fixed order and the first sweep (and its grid-wide sum) is skipped.
+// Each sweep's grid-wide sum is one counted arrival (grid_sum); the norm's sum is taken by the last
+// block to arrive, which finishes the step while the others leave.  A thread's elements are the same
+// in every sweep, so w needs no grid-wide ordering between sweeps.
 __global__ void __launch_bounds__(kCtlThreads) k_mgs_step(GmresState* gs, const double2* __restrict__ V,
                                                          long long ldv, double2* __restrict__ w, long long N,
                                                          double* partials, GridBarrier* bar, SolveCfg cfg,
                                                          cudaGraphConditionalHandle h_inner, int set_cond,
                                                          const double* __restrict__ pre_part, int pre_n) {
-  __shared__ double sh[32];
+  __shared__ double sh[33];
+  __shared__ double hc[kMaxM + 1];  // column j of H before the rotations (h_0j .. h_jj)
   const int j = gs->j;
   const int nb = gridDim.x;
+  const long long start = (long long)blockIdx.x * blockDim.x + threadIdx.x, stride = (long long)nb * blockDim.x;
   double hprev = 0.0;
-  double nrm2 = 0.0;
   int i0 = 0;
   if (pre_n > 0) {
     double v = 0.0;
     for (int b = threadIdx.x; b < pre_n; b += blockDim.x) v += pre_part[b];
     v = block_sum_c(v, sh);
-    __shared__ double bc0;
-    if (threadIdx.x == 0) bc0 = v;
+    if (threadIdx.x == 0) sh[32] = v;
     __syncthreads();
-    hprev = bc0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) gs->H[(size_t)j * (kMaxM + 1)] = hprev;
+    hprev = sh[32];
     i0 = 1;
   }
-  for (int i = i0; i <= j + 1; ++i) {
-    double* buf = partials + (size_t)(i & 1) * nb;
-    const double2* vi = (i <= j) ? V + (size_t)i * ldv : nullptr;
+  if (threadIdx.x == 0) hc[0] = hprev;
+  for (int i = i0; i <= j; ++i) {
     const double2* vp = (i > 0) ? V + (size_t)(i - 1) * ldv : nullptr;
-    double acc = mgs_sweep(w, vi, vp, hprev, N, (long long)blockIdx.x * blockDim.x + threadIdx.x,
-                           (long long)nb * blockDim.x);
-    acc = block_sum_c(acc, sh);
-    if (i == j + 1 && nb > 1) {
-      // the norm: only one thread needs it, so the last block to arrive sums the partials and
-      // finishes the step while the others leave (no wait)
-      __shared__ bool last_blk;
-      if (threadIdx.x == 0) {
-        buf[blockIdx.x] = acc;
-        __threadfence();
-        last_blk = (atomicAdd(&bar->done, 1u) == (unsigned)nb - 1u);
-      }
-      __syncthreads();
-      if (!last_blk) return;
-      __threadfence();
-      nrm2 = fixed_sum(buf, nb, sh);
-      if (threadIdx.x == 0) bar->done = 0u;
-      break;
-    }
-    if (threadIdx.x == 0) buf[blockIdx.x] = acc;
-    __threadfence();
-    grid_barrier(bar, &gs->err);
-    const double s = fixed_sum(buf, nb, sh);
-    if (i <= j) {
-      hprev = s;
-      if (blockIdx.x == 0 && threadIdx.x == 0) gs->H[(size_t)j * (kMaxM + 1) + i] = s;
-    } else {
-      nrm2 = s;
-    }
+    const double acc = mgs_sweep(w, V + (size_t)i * ldv, vp, hprev, N, start, stride);
+    hprev = grid_sum(acc, partials + (size_t)(i & 1) * nb, &bar->count, (unsigned)(i - i0 + 1) * (unsigned)nb,
+                     &gs->err, sh);
+    if (threadIdx.x == 0) hc[i] = hprev;
   }
-  if (threadIdx.x != 0) return;  // one block is left: the last to arrive (or the only one)
-  givens_finish(gs, j, nrm2, w, cfg, h_inner, set_cond);
-}
-
-// The end of Arnoldi step j (one thread): h_{j+1,j} = sqrt(nrm2), the previous rotations on column j,
-// the new rotation, g, the convergence test, the state for the next column and, if set_cond, the
-// inner-loop condition.
-__device__ __forceinline__ void givens_finish(GmresState* gs, int j, double nrm2, double2* w, const SolveCfg& cfg,
-                                              cudaGraphConditionalHandle h_inner, int set_cond) {
-  double* Hc = gs->H + (size_t)j * (kMaxM + 1);
-  const double hnext = sqrt(nrm2);
-  Hc[j + 1] = hnext;
-  for (int i = 0; i < j; ++i) {  // previous rotations
-    const double t = gs->cs[i] * Hc[i] + gs->sn[i] * Hc[i + 1];
-    Hc[i + 1] = -gs->sn[i] * Hc[i] + gs->cs[i] * Hc[i + 1];
-    Hc[i] = t;
+  // the norm sweep: w -= h_jj v_j, ||w||^2
+  const double acc = mgs_sweep(w, nullptr, V + (size_t)j * ldv, hprev, N, start, stride);
+  double nrm2;
+  if (!grid_sum_last(acc, partials + (size_t)((j + 1) & 1) * nb, &bar->done, &bar->count, sh, &nrm2)) return;
+  if (threadIdx.x < 32) {
+    const int cont = givens_finish_warp(gs, j, nrm2, hc, w, cfg);
+    if (threadIdx.x == 0 && set_cond) cudaGraphSetConditional(h_inner, cont ? 1u : 0u);
   }
-  const double rr = hypot(Hc[j], Hc[j + 1]);
-  const double c = Hc[j] / rr, sn = Hc[j + 1] / rr;
-  gs->cs[j] = c;
-  gs->sn[j] = sn;
-  Hc[j] = rr;
-  Hc[j + 1] = 0.0;
-  gs->g[j + 1] = -sn * gs->g[j];
-  gs->g[j] = c * gs->g[j];
-  const double rel = fabs(gs->g[j + 1]) / gs->ref;
-  gs->relres = rel;
-  gs->inv_h = (hnext > 0.0) ? 1.0 / hnext : 0.0;
-  int done = 0;
-  if (!isfinite(rel) || !isfinite(hnext)) done = 3;
-  else if (rel < gs->tol) done = 1;
-  else if (hnext == 0.0) done = 2;
-  gs->done = done;
-  gs->it += 1;
-  gs->j = j + 1;
-  gs->src = w;
-  gs->src_scale = gs->inv_h;
-  const int stop = done != 0 || gs->it >= cfg.max_it || gs->err;
-  gs->no_restart = stop;
-  if (set_cond) cudaGraphSetConditional(h_inner, (!stop && j + 1 < cfg.m) ? 1u : 0u);
 }
 
 // The same Arnoldi step on one thread-block cluster of CL CTAs (small grids: a sweep moves a few MB
@@ -135,14 +76,15 @@ __global__ void __launch_bounds__(kClThreads) k_mgs_cluster(GmresState* gs, cons
   __shared__ double sh[32];
   __shared__ double part[2];  // this CTA's partial of the current sweep (by sweep parity)
   __shared__ double bc;
+  __shared__ double hc[kMaxM + 1];  // column j of H before the rotations (h_0j .. h_jj)
   const int j = gs->j;
   double hprev = 0.0, nrm2 = 0.0;
   int i0 = 0;
   if (pre_n > 0) {
     hprev = fixed_sum(pre_part, pre_n, sh);
-    if (rank == 0 && threadIdx.x == 0) gs->H[(size_t)j * (kMaxM + 1)] = hprev;
     i0 = 1;
   }
+  if (threadIdx.x == 0) hc[0] = hprev;
   for (int i = i0; i <= j + 1; ++i) {
     const double2* vi = (i <= j) ? V + (size_t)i * ldv : nullptr;
     const double2* vp = (i > 0) ? V + (size_t)(i - 1) * ldv : nullptr;
@@ -161,13 +103,16 @@ __global__ void __launch_bounds__(kClThreads) k_mgs_cluster(GmresState* gs, cons
     __syncthreads();
     if (i <= j) {
       hprev = sum;
-      if (rank == 0 && threadIdx.x == 0) gs->H[(size_t)j * (kMaxM + 1) + i] = sum;
+      if (threadIdx.x == 0) hc[i] = sum;
     } else {
       nrm2 = sum;
     }
   }
   cl.sync();  // no CTA leaves while another may still read its shared memory
-  if (rank == 0 && threadIdx.x == 0) givens_finish(gs, j, nrm2, w, cfg, h_inner, set_cond);
+  if (rank == 0 && threadIdx.x < 32) {
+    const int cont = givens_finish_warp(gs, j, nrm2, hc, w, cfg);
+    if (threadIdx.x == 0 && set_cond) cudaGraphSetConditional(h_inner, cont ? 1u : 0u);
+  }
 }
 
 // ||x|| into gs (beta, 1/beta, g = beta e_1), fixed-order reduction; then, by mode:
@@ -592,10 +537,13 @@ void launch_resid_update(const double2* V, long long ldv, const double2* w, cons
   k_resid_update<<<ew_blocks_c(N), 256, 0, s>>>(V, ldv, w, gs, k, r, N, nrm_part);
 }
 
-// Self-test of the bounded wait: one block arrives at a grid barrier whose arrival count is preset so
-// that the barrier can never complete (a release that nothing performs); grid_barrier must give up
-// after kMaxSpin polls, record the failure and return.
-__global__ void k_selftest_wait(GridBarrier* b, int* err) { grid_barrier_global(b, err); }
+// Self-test of the bounded wait: the single block of this launch arrives and then waits for the
+// arrival of a second block, which does not exist (a release that nothing performs); the wait must
+// give up after kMaxSpin polls, record the failure and return.
+__global__ void k_selftest_wait(GridBarrier* b, int* err) {
+  if (threadIdx.x == 0) red_add_release(&b->count, 1u);
+  warp_wait_count(&b->count, 2u, err);
+}
 
 }  // namespace rfnse
 
@@ -607,7 +555,7 @@ extern "C" int rfnse_selftest_bounded_wait(void* stream, int* err, double* ms) {
   int* d_err = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int st = RFNSE_OK;
-  const GridBarrier init = {1u, 0u};  // one phantom arrival: the single block's arrival makes 2 of 1
+  const GridBarrier init = {0u, 0u};
   if (cudaMalloc(&b, sizeof(GridBarrier)) != cudaSuccess || cudaMalloc(&d_err, sizeof(int)) != cudaSuccess ||
       cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     st = RFNSE_ENOMEM;

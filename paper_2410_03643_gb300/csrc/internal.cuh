@@ -122,11 +122,11 @@ struct TableArena {
 
 struct ParamRecord;  // passes.cuh: a pass's parameters and its batched launcher (lock-step capture)
 
-// Counter and generation of a grid-wide barrier (control.cu); zero-initialised.
+// Arrival counters of the cooperative kernels' grid-wide sums (coop.cuh); zero-initialised, and zero
+// again when a launch ends (cleared by its last block).
 struct GridBarrier {
-  unsigned count;
-  unsigned gen;
-  unsigned done;  // arrivals at the Arnoldi kernel's last reduction (reset by the last block)
+  unsigned count;  // arrivals at the grid-wide sums of the current launch
+  unsigned done;   // arrivals at the launch's last sum
 };
 
 // ---- device-side control (control.cu) -----------------------------------------------------------

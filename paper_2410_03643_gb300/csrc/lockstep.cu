@@ -169,7 +169,8 @@ __global__ void k_ls_cycle_begin(const LockInst* __restrict__ li, int n, unsigne
 __global__ void __launch_bounds__(kCtlThreads) k_ls_mgs(const LockInst* __restrict__ li, int n, GridBarrier* bar,
                                                         unsigned* done_all, unsigned long long* counts,
                                                         cudaGraphConditionalHandle h_inner) {
-  __shared__ double sh[32];
+  __shared__ double sh[33];
+  __shared__ double hc[kMaxM + 1];  // this instance's column j of H before the rotations
   __shared__ int s_inst, s_jmax, s_first;
   if (threadIdx.x == 0) {
     const int b = blockIdx.x;
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(kCtlThreads) k_ls_mgs(const LockInst* __restri
       else hi = mid - 1;
     }
     s_inst = lo;
-    // read before this block's first barrier: the finishing blocks write j and iskip only after the
+    // read before this block's first arrival: the finishing blocks write j and iskip only after the
     // last one, which no block passes before every block has made these reads
     int jm = -1, first = 1;
     for (int k = 0; k < n; ++k)
@@ -204,9 +205,12 @@ __global__ void __launch_bounds__(kCtlThreads) k_ls_mgs(const LockInst* __restri
   int i0 = 0;
   if (active && I.dot_n > 0) {  // h_0j from the partials the product pass left (same sum in every block)
     hprev = fixed_sum(I.dot_part, I.dot_n, sh);
-    if (lb == 0 && threadIdx.x == 0) gs->H[(size_t)j * (kMaxM + 1)] = hprev;
     i0 = 1;
   }
+  if (threadIdx.x == 0) hc[0] = hprev;
+  // Sweep i of every instance between two counted arrivals of the whole grid (coop.cuh); each
+  // instance sums only its own blocks' partials.
+  unsigned arrivals = 0;
   for (int i = s_first; i <= jmax + 1; ++i) {  // sweep 0 only when some instance needs it
     const bool mine = active && i >= i0 && i <= j + 1;  // uniform in the block
     double acc = 0.0;
@@ -215,59 +219,38 @@ __global__ void __launch_bounds__(kCtlThreads) k_ls_mgs(const LockInst* __restri
       const double2* vp = (i > 0) ? I.V + (size_t)(i - 1) * N : nullptr;
       acc = mgs_sweep(w, vi, vp, hprev, N, (long long)lb * blockDim.x + threadIdx.x, (long long)nb * blockDim.x);
     }
-    acc = block_sum_c(acc, sh);
+    const double b = block_partial_w0(acc, sh);
     double* buf = I.cpart + (size_t)(i & 1) * nb;
-    if (mine && threadIdx.x == 0) buf[lb] = acc;
-    __threadfence();
-    grid_barrier(bar, &gs->err);
+    ++arrivals;
+    if (threadIdx.x < 32) {
+      if (threadIdx.x == 0) {
+        if (mine) buf[lb] = b;
+        red_add_release(&bar->count, 1u);
+      }
+      warp_wait_count(&bar->count, arrivals * gridDim.x, &gs->err);
+      const double t = mine ? warp_sum_partials(buf, nb) : 0.0;
+      if (threadIdx.x == 0) sh[32] = t;
+    }
+    __syncthreads();
     if (mine) {
-      const double s = fixed_sum(buf, nb, sh);
+      const double t = sh[32];
       if (i <= j) {
-        hprev = s;
-        if (lb == 0 && threadIdx.x == 0) gs->H[(size_t)j * (kMaxM + 1) + i] = s;
+        hprev = t;
+        if (threadIdx.x == 0) hc[i] = t;
       } else {
-        nrm2 = s;
+        nrm2 = t;
       }
     }
   }
-  if (active && lb == 0 && threadIdx.x == 0) {  // Givens update and test of this instance
-    const SolveCfg cfg = I.cfg;
-    double* Hc = gs->H + (size_t)j * (kMaxM + 1);
-    const double hnext = sqrt(nrm2);
-    Hc[j + 1] = hnext;
-    for (int i = 0; i < j; ++i) {
-      const double t = gs->cs[i] * Hc[i] + gs->sn[i] * Hc[i + 1];
-      Hc[i + 1] = -gs->sn[i] * Hc[i] + gs->cs[i] * Hc[i + 1];
-      Hc[i] = t;
-    }
-    const double rr = hypot(Hc[j], Hc[j + 1]);
-    const double c = Hc[j] / rr, sn = Hc[j + 1] / rr;
-    gs->cs[j] = c;
-    gs->sn[j] = sn;
-    Hc[j] = rr;
-    Hc[j + 1] = 0.0;
-    gs->g[j + 1] = -sn * gs->g[j];
-    gs->g[j] = c * gs->g[j];
-    const double rel = fabs(gs->g[j + 1]) / gs->ref;
-    gs->relres = rel;
-    gs->inv_h = (hnext > 0.0) ? 1.0 / hnext : 0.0;
-    int done = 0;
-    if (!isfinite(rel) || !isfinite(hnext)) done = 3;
-    else if (rel < gs->tol) done = 1;
-    else if (hnext == 0.0) done = 2;
-    gs->done = done;
-    gs->it += 1;
-    gs->j = j + 1;
-    gs->src = w;
-    gs->src_scale = gs->inv_h;
-    const int stop = done != 0 || gs->it >= cfg.max_it || gs->err;
-    gs->no_restart = stop;
-    I.fl->iskip = (!stop && j + 1 < cfg.m) ? 0 : 1;
+  if (active && lb == 0 && threadIdx.x < 32) {  // Givens update and test of this instance
+    const int cont = givens_finish_warp(gs, j, nrm2, hc, w, I.cfg);
+    if (threadIdx.x == 0) I.fl->iskip = cont ? 0 : 1;
   }
   __shared__ bool last;
   if (threadIdx.x == 0) last = last_to_arrive(done_all);
   __syncthreads();
   if (last && threadIdx.x == 0) {
+    bar->count = 0u;  // every block has passed its last wait: clear the arrivals for the next launch
     int any = 0;
     for (int k = 0; k < n; ++k) any |= !((volatile LockFlags*)li[k].fl)->iskip;
     cudaGraphSetConditional(h_inner, any ? 1u : 0u);
