@@ -14,6 +14,10 @@ template <> struct cvec<float> {
   static __host__ __device__ __forceinline__ float2 make(float a, float b) { return make_float2(a, b); }
 };
 template <typename R> using cv = typename cvec<R>::type;
+// the real type of a complex type
+template <typename V> struct creal {
+  using type = decltype(V().x);
+};
 
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -42,6 +46,8 @@ __device__ __forceinline__ double2 cmul_i(double2 a) { return make_double2(-a.y,
 __device__ __forceinline__ float2 cmul_i(float2 a) { return make_float2(-a.y, a.x); }
 __device__ __forceinline__ double2 cmul_mi(double2 a) { return make_double2(a.y, -a.x); }
 __device__ __forceinline__ float2 cmul_mi(float2 a) { return make_float2(a.y, -a.x); }
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 
 // conversions between storage and compute precision
 template <typename R> __device__ __forceinline__ cv<R> to_c(double2 v);

@@ -74,26 +74,101 @@ __device__ __forceinline__ dfl df_split(double x) {
 }
 __device__ __forceinline__ double df_to_double(dfl a) { return df_f2d(a.hi) + df_f2d(a.lo); }
 
-// complex double-float
+// Packed float pairs (sm_100 family): one instruction applies the same FP32 operation, rounded to
+// nearest on its own, to both halves; per component the result is that of the scalar _rn operation.
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
+      "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+      "sub.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 f2_bcast(float v) { return make_float2(v, v); }
+
+// complex double-float, stored as the pairs hi = (re.hi, im.hi) and lo = (re.lo, im.lo), so that the
+// real and imaginary parts go through every step of an operation together as packed pairs: the same
+// operations, in the same order, as the scalar double-float arithmetic above on each part.
 struct cdf {
-  dfl x, y;
+  float2 hi, lo;
 };
 template <> struct cvec<dfl> {
   using type = cdf;
-  static __host__ __device__ __forceinline__ cdf make(dfl a, dfl b) { return cdf{a, b}; }
+  static __host__ __device__ __forceinline__ cdf make(dfl a, dfl b) {
+    return cdf{make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)};
+  }
+};
+template <> struct creal<cdf> {
+  using type = dfl;
 };
 
-__device__ __forceinline__ cdf cadd(cdf a, cdf b) { return cdf{a.x + b.x, a.y + b.y}; }
-__device__ __forceinline__ cdf csub(cdf a, cdf b) { return cdf{a.x - b.x, a.y - b.y}; }
-__device__ __forceinline__ cdf cneg(cdf a) { return cdf{-a.x, -a.y}; }
-__device__ __forceinline__ cdf cmul(cdf a, cdf b) { return cdf{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
-__device__ __forceinline__ cdf cscale(cdf a, dfl s) { return cdf{a.x * s, a.y * s}; }
-__device__ __forceinline__ cdf cmul_i(cdf a) { return cdf{-a.y, a.x}; }
-__device__ __forceinline__ cdf cmul_mi(cdf a) { return cdf{a.y, -a.x}; }
-__device__ __forceinline__ cdf cdf_from(double2 v) { return cdf{df_split(v.x), df_split(v.y)}; }
-// storage of a complex double-float as (re.hi, re.lo, im.hi, im.lo)
-__device__ __forceinline__ cdf cdf_ld(float4 q) { return cdf{dfl(q.x, q.y), dfl(q.z, q.w)}; }
-__device__ __forceinline__ float4 cdf_st(cdf v) { return make_float4(v.x.hi, v.x.lo, v.y.hi, v.y.lo); }
-__device__ __forceinline__ double2 cdf_to(cdf v) { return make_double2(df_to_double(v.x), df_to_double(v.y)); }
+// TwoSum and FastTwoSum on pairs; a + b and a - b of double-float pairs (operator+ above per part)
+__device__ __forceinline__ cdf cadd(cdf a, cdf b) {
+  const float2 s = f2_add(a.hi, b.hi);
+  const float2 bb = f2_sub(s, a.hi);
+  const float2 e = f2_add(f2_sub(a.hi, f2_sub(s, bb)), f2_sub(b.hi, bb));
+  const float2 t = f2_add(e, f2_add(a.lo, b.lo));
+  const float2 s2 = f2_add(s, t);
+  return cdf{s2, f2_sub(t, f2_sub(s2, s))};
+}
+__device__ __forceinline__ cdf csub(cdf a, cdf b) {  // a + (-b): -b - bb = -(b + bb)
+  const float2 s = f2_sub(a.hi, b.hi);
+  const float2 bb = f2_sub(s, a.hi);
+  const float2 e = f2_sub(f2_sub(a.hi, f2_sub(s, bb)), f2_add(b.hi, bb));
+  const float2 t = f2_add(e, f2_sub(a.lo, b.lo));
+  const float2 s2 = f2_add(s, t);
+  return cdf{s2, f2_sub(t, f2_sub(s2, s))};
+}
+// (x.hi + x.lo) times each component of the pair (bh + bl): TwoProd by FMA with the cross terms, then
+// FastTwoSum (operator* above per part).  With q = fl(-x.hi bh) = -p exactly: e = fma(x.hi, bh, q),
+// s = fl(e - q) = fl(p + e), e' = e - (s + q) = e - (s - p).
+__device__ __forceinline__ cdf df_scale_pair(float xh, float xl, float2 bh, float2 bl) {
+  const float2 xh2 = f2_bcast(xh);
+  const float2 q = f2_mul(f2_bcast(-xh), bh);
+  float2 e = f2_fma(xh2, bh, q);
+  e = f2_fma(xh2, bl, e);
+  e = f2_fma(f2_bcast(xl), bh, e);
+  const float2 s = f2_sub(e, q);
+  return cdf{s, f2_sub(e, f2_add(s, q))};
+}
+__device__ __forceinline__ cdf cneg(cdf a) {
+  return cdf{make_float2(-a.hi.x, -a.hi.y), make_float2(-a.lo.x, -a.lo.y)};
+}
+// a b = (a.re b.re - a.im b.im, a.re b.im + a.im b.re): the pairs a.re (b.re, b.im) and
+// a.im (b.im, b.re), then one pair addition with the first component of the second negated
+__device__ __forceinline__ cdf cmul(cdf a, cdf b) {
+  const cdf x = df_scale_pair(a.hi.x, a.lo.x, b.hi, b.lo);
+  const cdf y = df_scale_pair(a.hi.y, a.lo.y, make_float2(b.hi.y, b.hi.x), make_float2(b.lo.y, b.lo.x));
+  return cadd(x, cdf{make_float2(-y.hi.x, y.hi.y), make_float2(-y.lo.x, y.lo.y)});
+}
+__device__ __forceinline__ cdf cscale(cdf a, dfl s) {  // (a.re s, a.im s)
+  const float2 sh = f2_bcast(s.hi);
+  const float2 q = f2_mul(make_float2(-a.hi.x, -a.hi.y), sh);
+  float2 e = f2_fma(a.hi, sh, q);
+  e = f2_fma(a.hi, f2_bcast(s.lo), e);
+  e = f2_fma(a.lo, sh, e);
+  const float2 r = f2_sub(e, q);
+  return cdf{r, f2_sub(e, f2_add(r, q))};
+}
+__device__ __forceinline__ cdf cmul_i(cdf a) {
+  return cdf{make_float2(-a.hi.y, a.hi.x), make_float2(-a.lo.y, a.lo.x)};
+}
+__device__ __forceinline__ cdf cmul_mi(cdf a) {
+  return cdf{make_float2(a.hi.y, -a.hi.x), make_float2(a.lo.y, -a.lo.x)};
+}
+__device__ __forceinline__ cdf cconj(cdf a) {
+  return cdf{make_float2(a.hi.x, -a.hi.y), make_float2(a.lo.x, -a.lo.y)};
+}
+__device__ __forceinline__ cdf cdf_from(double2 v) { return cvec<dfl>::make(df_split(v.x), df_split(v.y)); }
+// storage of a complex double-float as (re.hi, im.hi, re.lo, im.lo)
+__device__ __forceinline__ cdf cdf_ld(float4 q) { return cdf{make_float2(q.x, q.y), make_float2(q.z, q.w)}; }
+__device__ __forceinline__ float4 cdf_st(cdf v) { return make_float4(v.hi.x, v.hi.y, v.lo.x, v.lo.y); }
+__device__ __forceinline__ double2 cdf_to(cdf v) {
+  return make_double2(df_to_double(dfl(v.hi.x, v.lo.x)), df_to_double(dfl(v.hi.y, v.lo.y)));
+}
 
 }  // namespace rfnse

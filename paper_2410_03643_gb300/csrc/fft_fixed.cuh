@@ -190,6 +190,12 @@ __device__ __forceinline__ void dft_r(V (&v)[RAD]) {
   }
 }
 
+// Padded offset of element i + d from that of element i, d a compile-time step: every stage reads
+// j + r NB (NB a multiple of 16) and writes base + r NS with base a multiple of RAD NS plus k < NS, and
+// for these (i mod 16) + (d mod 16) < 16, so fft_pad(i + d) = fft_pad(i) + d + (d >> 4) and the r-th
+// access of a butterfly is a constant offset from its first.
+__host__ __device__ constexpr int pad_step(int d) { return d + (d >> 4); }
+
 // One Stockham stage of radix RAD on sub-transforms of length NS: L/RAD butterflies, Q per thread.
 template <int L, int RAD, int NS, int T, bool INV, bool ZU, bool HO, typename V, typename R>
 __device__ __forceinline__ void fixed_stage(V* x, const V* seg, int lt) {
@@ -201,16 +207,17 @@ __device__ __forceinline__ void fixed_stage(V* x, const V* seg, int lt) {
     const int j = lt + q * T;
     if (j < NB) {
       const int k = j & (NS - 1);
+      const V* xj = x + fft_pad(j);
 #pragma unroll
       for (int r = 0; r < RAD; ++r) {
         if (ZU && 2 * r >= RAD) v[q][r] = cvec<R>::make((R)0, (R)0);
-        else v[q][r] = x[fft_pad(j + r * NB)];
+        else v[q][r] = xj[pad_step(r * NB)];
       }
       if (NS > 1) {
 #pragma unroll
         for (int r = 1; r < RAD; ++r) {
           V w = seg[(r - 1) * NS + k];
-          if (INV) w.y = -w.y;
+          if (INV) w = cconj(w);
           v[q][r] = cmul(v[q][r], w);
         }
       }
@@ -223,11 +230,11 @@ __device__ __forceinline__ void fixed_stage(V* x, const V* seg, int lt) {
     const int j = lt + q * T;
     if (j < NB) {
       const int k = j & (NS - 1);
-      const int base = (j - k) * RAD + k;
+      V* xb = x + fft_pad((j - k) * RAD + k);
 #pragma unroll
       for (int r = 0; r < RAD; ++r) {
         if (HO && 2 * r >= RAD) continue;
-        x[fft_pad(base + r * NS)] = v[q][permr<RAD>(r)];
+        xb[pad_step(r * NS)] = v[q][permr<RAD>(r)];
       }
     }
   }
@@ -249,7 +256,7 @@ __device__ __forceinline__ void fixed_stages(V* x, const V* seg, int lt) {
 // FFT of every line of the tile (B lines, line stride Lp).  Threads beyond B * T wait at the barriers.
 template <int LOG2L, int LOGR, bool INV, bool ZU, bool HO, typename V>
 __device__ __forceinline__ void fft_lines_fixed(V* buf, int Lp, int B, const V* tw) {
-  using R = decltype(V().x);
+  using R = typename creal<V>::type;
   using P = FixedPlan<LOG2L, LOGR>;
   constexpr int NST = P::NFULL + (P::LOGLAST ? 1 : 0);
   const int line = threadIdx.x / P::T;

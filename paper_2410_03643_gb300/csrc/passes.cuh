@@ -98,7 +98,7 @@ struct PassParams {
   // double-float Toeplitz passes: when set, each block's share of ||result||^2
   double* nrm_part;
   // double-float Toeplitz passes of a product along several axes: the input split into double-float
-  // once, written by the first pass and read by the others (float4 per point: re.hi, re.lo, im.hi,
+  // once, written by the first pass and read by the others (float4 per point: re.hi, im.hi, re.lo,
   // im.lo); null when not used
   const void* dfz_in;
   void* dfz_out;
@@ -221,6 +221,52 @@ __device__ __forceinline__ void pass_work_item(const PassWork& w, PassParams& ps
   __syncthreads();
 }
 
+// The elements e = tid, tid + nthr, ... < B n of a tile, visited in that order without a division or a
+// 64-bit multiply per element: (line l, position pos) and the global index g are stepped.  Strided
+// axes: e = pos B + l, and nthr is a multiple of B, so l is fixed and pos, g advance by constant
+// steps.  x-lines: g = line0 n + e is contiguous; with several lines per tile, pos wraps into the
+// next line (nthr / n + 1 wraps at most per step).
+struct TileWalk {
+  int l, pos;         // line of the tile and position along it
+  long long g;        // global index of the element
+  bool valid;         // its line exists in the grid
+  int n, B, dpos;     // axis extent, lines per tile, position step (strided axes)
+  long long dg;       // global step
+  bool xax;
+  long long line0, nlines;
+  __device__ __forceinline__ TileWalk(const PassParams& p, bool xax_, int tid, int nthr, long long line0_,
+                                      long long hi, long long lo0)
+      : n(p.n), B(p.B), xax(xax_), line0(line0_), nlines(p.nlines) {
+    if (xax) {
+      l = (B == 1) ? 0 : tid / n;
+      pos = tid - l * n;
+      g = line0 * n + tid;
+      dg = nthr;
+      dpos = nthr;
+      valid = line0 + l < nlines;
+    } else {
+      l = tid & (B - 1);
+      pos = tid >> p.log2B;
+      dpos = nthr >> p.log2B;
+      g = lo0 + l + (long long)pos * p.stride + hi * p.stride * n;
+      dg = (long long)dpos * p.stride;
+      valid = lo0 + l < p.stride;
+    }
+  }
+  __device__ __forceinline__ bool more() const { return xax ? (pos < n && l < B) : pos < n; }
+  __device__ __forceinline__ void next() {
+    pos += dpos;
+    g += dg;
+    if (xax && B > 1) {
+      while (pos >= n) {
+        pos -= n;
+        ++l;
+      }
+      valid = line0 + l < nlines;
+    }
+  }
+};
+
 template <typename R, typename TIN, typename TOUT, typename TACCI, typename TACCO, int FLAGS, int LOG2L>
 __device__ __forceinline__ void line_pass_body(const PassParams& p, const long long tile) {
   using V = cv<R>;
@@ -246,28 +292,6 @@ __device__ __forceinline__ void line_pass_body(const PassParams& p, const long l
     hi = tile / p.tiles_inner;
     lo0 = (tile - hi * p.tiles_inner) * B;
   }
-  // element e of the tile -> (line l, position pos), ordered for coalesced global access
-  // (B is a power of two; a tile of x-lines of the large transforms is a single line)
-  const int log2B = p.log2B;
-  auto map = [&](int e, int& l, int& pos) {
-    if (xax) {
-      if (B == 1) { l = 0; pos = e; }
-      else { l = e / n; pos = e - l * n; }
-    } else {
-      pos = e >> log2B;
-      l = e & (B - 1);
-    }
-  };
-  auto gidx = [&](int l, int pos, bool& valid) -> long long {
-    if (xax) {
-      const long long ln = line0 + l;
-      valid = ln < p.nlines;
-      return ln * n + pos;
-    }
-    const long long lo = lo0 + l;
-    valid = lo < p.stride;
-    return lo + (long long)pos * p.stride + hi * p.stride * n;
-  };
   auto at = [&](int l, int i) -> V& { return buf[(size_t)l * Lp + fft_pad(i)]; };
 
   // ---- load -----------------------------------------------------------------------------------
@@ -285,11 +309,10 @@ __device__ __forceinline__ void line_pass_body(const PassParams& p, const long l
       sc = *p.in_scale;
     }
   }
-  for (int e = tid; e < B * n; e += nthr) {
-    int l, pos;
-    map(e, l, pos);
-    bool valid;
-    const long long g = gidx(l, pos, valid);
+  for (TileWalk it(p, xax, tid, nthr, line0, hi, lo0); it.more(); it.next()) {
+    const int l = it.l, pos = it.pos;
+    const bool valid = it.valid;
+    const long long g = it.g;
     V v = zero;
     if (valid) {
       if (FLAGS & F_INSCALE) {
@@ -314,10 +337,7 @@ __device__ __forceinline__ void line_pass_body(const PassParams& p, const long l
     at(l, Nh) = zero;
   }
   if (!(FLAGS & F_DST) || (FLAGS & F_CIRC)) {      // zero padding of the circulant embedding
-    for (int e = tid; e < B * (Nh - 1); e += nthr) {
-      const int l = e / (Nh - 1);
-      at(l, Nh + 1 + (e - l * (Nh - 1))) = zero;
-    }
+    for (int e = tid; e < B * Nh; e += nthr) at(e >> (p.log2L - 1), Nh + (e & (Nh - 1))) = zero;  // Nh .. L-1
   }
   __syncthreads();
 
@@ -328,11 +348,10 @@ __device__ __forceinline__ void line_pass_body(const PassParams& p, const long l
     bluestein_lines<R, LOG2L>(buf, Lp, L, p.log2L, p.nt, tws, n, B, p.chirp, p.bspec,
                               (FLAGS & F_LAM) ? false : p.inv_dft != 0);
     if (FLAGS & F_LAM) {
-      for (int e = tid; e < B * n; e += nthr) {
-        int l, pos;
-        map(e, l, pos);
-        bool valid;
-        const long long g = gidx(l, pos, valid);
+      for (TileWalk it(p, xax, tid, nthr, line0, hi, lo0); it.more(); it.next()) {
+        const int l = it.l, pos = it.pos;
+        const bool valid = it.valid;
+        const long long g = it.g;
         const V f = valid ? ld_c<R>(p.lamfac, g) : zero;   // mode index = grid index on this axis
         at(l, 1 + pos) = cmul(at(l, 1 + pos), f);
       }
@@ -345,11 +364,10 @@ __device__ __forceinline__ void line_pass_body(const PassParams& p, const long l
   if ((FLAGS & F_DST) && !(FLAGS & F_CIRC)) {
     fft_any<LOG2L, false, false, false>(buf, Lp, L, p.log2L, p.nt, B, tws);
     if (FLAGS & F_LAM) {
-      for (int e = tid; e < B * n; e += nthr) {
-        int l, pos;
-        map(e, l, pos);
-        bool valid;
-        const long long g = gidx(l, pos, valid);
+      for (TileWalk it(p, xax, tid, nthr, line0, hi, lo0); it.more(); it.next()) {
+        const int l = it.l, pos = it.pos;
+        const bool valid = it.valid;
+        const long long g = it.g;
         const int k = pos + 1;                     // sine mode k = 1..n along this axis
         const V f = valid ? ld_c<R>(p.lamfac, g) : zero;
         at(l, k) = cmul(at(l, k), f);
@@ -367,22 +385,20 @@ __device__ __forceinline__ void line_pass_body(const PassParams& p, const long l
   // ---- DST output / D sub-solve ---------------------------------------------------------------
   if ((FLAGS & F_DST) && !(FLAGS & F_DSCALE)) {
     TOUT* out = reinterpret_cast<TOUT*>(p.out);
-    for (int e = tid; e < B * n; e += nthr) {
-      int l, pos;
-      map(e, l, pos);
-      bool valid;
-      const long long g = gidx(l, pos, valid);
+    for (TileWalk it(p, xax, tid, nthr, line0, hi, lo0); it.more(); it.next()) {
+      const int l = it.l, pos = it.pos;
+      const bool valid = it.valid;
+      const long long g = it.g;
       if (valid) st_c(out + g, (FLAGS & F_CIRC) ? at(l, 1 + pos) : cmul_i(cscale(at(l, 1 + pos), dsc)));
     }
   }
   if (FLAGS & F_DSCALE) {
     TOUT* out = reinterpret_cast<TOUT*>(p.out);
     if (p.gdyn && p.zbase) out = reinterpret_cast<TOUT*>(p.zbase) + (long long)p.gdyn->j * p.ldv;
-    for (int e = tid; e < B * n; e += nthr) {
-      int l, pos;
-      map(e, l, pos);
-      bool valid;
-      const long long g = gidx(l, pos, valid);
+    for (TileWalk it(p, xax, tid, nthr, line0, hi, lo0); it.more(); it.next()) {
+      const int l = it.l, pos = it.pos;
+      const bool valid = it.valid;
+      const long long g = it.g;
       V z = zero;
       if (valid) {
         z = at(l, 1 + pos);                                   // identity preconditioner: the input
@@ -399,10 +415,7 @@ __device__ __forceinline__ void line_pass_body(const PassParams& p, const long l
       }
     }
     if (FLAGS & (F_TOEP_X | F_TOEP_ACC)) {
-      for (int e = tid; e < B * (Nh - 1); e += nthr) {
-        const int l = e / (Nh - 1);
-        at(l, Nh + 1 + (e - l * (Nh - 1))) = zero;
-      }
+      for (int e = tid; e < B * Nh; e += nthr) at(e >> (p.log2L - 1), Nh + (e & (Nh - 1))) = zero;  // Nh .. L-1
       for (int l = tid; l < B; l += nthr) {
         at(l, 0) = zero;
         at(l, Nh) = zero;
@@ -429,11 +442,10 @@ __device__ __forceinline__ void line_pass_body(const PassParams& p, const long l
     TACCO* accout = reinterpret_cast<TACCO*>(p.acc_out);
     const R* Dr = reinterpret_cast<const R*>(p.Dr);
     [[maybe_unused]] double dot = 0.0;
-    for (int e = tid; e < B * n; e += nthr) {
-      int l, pos;
-      map(e, l, pos);
-      bool valid;
-      const long long g = gidx(l, pos, valid);
+    for (TileWalk it(p, xax, tid, nthr, line0, hi, lo0); it.more(); it.next()) {
+      const int l = it.l, pos = it.pos;
+      const bool valid = it.valid;
+      const long long g = it.g;
       if (!valid) continue;
       V t = at(l, 1 + pos);
       V acc = accin ? to_c<R>(accin[g]) : zero;
@@ -490,7 +502,8 @@ __device__ __forceinline__ void line_pass_fixed_body(const PassParams& p, const 
   constexpr bool TOEP = (FLAGS & (F_TOEP_X | F_TOEP_ACC)) != 0;
   if (p.skip && *p.skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = p.n, B = p.B;
+  constexpr int n = Nh - 1;  // the grids have n + 1 = L / 2 points per axis (a power of two)
+  const int B = p.B;
   const int Lp = fft_line_stride(L);
   V* buf = reinterpret_cast<V*>(smem_raw);
   V* tws = buf + (size_t)B * Lp;  // the L - 1 entries of the per-stage twiddle table
@@ -634,10 +647,7 @@ __device__ __forceinline__ void line_pass_fixed_body(const PassParams& p, const 
 #pragma unroll
     for (int q = 0; q < QN; ++q) {
       const int e = tid + q * nthr;
-      if (e < B * (Nh - 1)) {
-        const int l = e / (Nh - 1);
-        at(l, Nh + 1 + (e - l * (Nh - 1))) = zero;
-      }
+      if (e < B * Nh) at(e >> (LOG2L - 1), Nh + (e & (Nh - 1))) = zero;  // positions Nh .. L-1
     }
   }
   __syncthreads();
@@ -692,10 +702,7 @@ __device__ __forceinline__ void line_pass_fixed_body(const PassParams& p, const 
 #pragma unroll
       for (int q = 0; q < QN; ++q) {
         const int e = tid + q * nthr;
-        if (e < B * (Nh - 1)) {
-          const int l = e / (Nh - 1);
-          at(l, Nh + 1 + (e - l * (Nh - 1))) = zero;
-        }
+        if (e < B * Nh) at(e >> (LOG2L - 1), Nh + (e & (Nh - 1))) = zero;  // positions Nh .. L-1
       }
       for (int l = tid; l < B; l += nthr) {
         at(l, 0) = zero;
@@ -938,6 +945,7 @@ cudaError_t launch_pass_geom(rfnse_ctx* c, PassParams p, cudaStream_t s, const P
     return cudaErrorInvalidConfiguration;
   if (fixed ? (p.nt != (p.L >> kFixedLogR)) : (p.nt != p.L / 4 && p.nt != p.L / 8))
     return cudaErrorInvalidConfiguration;
+  if (p.L != 2 * (p.n + 1)) return cudaErrorInvalidConfiguration;  // the kernels index with n = L/2 - 1
   p.dst_scale_f = (float)p.dst_scale;
   p.ca_f = make_float2((float)p.ca.x, (float)p.ca.y);
   p.cb_f = make_float2((float)p.cb.x, (float)p.cb.y);
@@ -1100,6 +1108,8 @@ cudaError_t launch_pass_group(std::vector<PassParams>& ps, const PassGeom& gin, 
   if (g.B < 1 || (g.B & (g.B - 1)) != 0 || g.B * g.nt > kPassMaxThreads || g.B * g.nt < 1)
     return cudaErrorInvalidConfiguration;
   if (fixed ? (g.nt != (L >> kFixedLogR)) : (g.nt != L / 4 && g.nt != L / 8)) return cudaErrorInvalidConfiguration;
+  for (const PassParams& q : ps)
+    if (q.L != L || q.L != 2 * (q.n + 1)) return cudaErrorInvalidConfiguration;  // n = L/2 - 1 in the kernels
   std::vector<long long> start(ps.size() + 1, 0);
   grids.assign(ps.size(), 0);
   bool dot_fits = true;

@@ -41,13 +41,13 @@ __device__ __forceinline__ void toeplitz_df_body(const PassParams& p, const long
   if (p.skip && *p.skip) return;  // uniform
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int L = 1 << LOG2L;
-  constexpr int Nh = L >> 1;
-  const int n = p.n, B = p.B;
+  constexpr int Nh = L >> 1;  // the grids have n + 1 = L / 2 points per axis
+  const int B = p.B;
   const int Lp = fft_line_stride(L);
   V* buf = reinterpret_cast<V*>(smem_raw);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const bool xax = (p.stride == 1);
-  const V zero = cdf{dfl(0.0f, 0.0f), dfl(0.0f, 0.0f)};
+  const V zero = cdf{make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
 
   long long line0 = 0, hi = 0, lo0 = 0;
   if (xax) {
@@ -56,26 +56,7 @@ __device__ __forceinline__ void toeplitz_df_body(const PassParams& p, const long
     hi = tile / p.tiles_inner;
     lo0 = (tile - hi * p.tiles_inner) * B;
   }
-  // the tiling of k_line_pass: x lines contiguous, strided tiles of B lines adjacent in x
-  auto map = [&](int e, int& l, int& pos) {
-    if (xax) {
-      if (B == 1) { l = 0; pos = e; }
-      else { l = e / n; pos = e - l * n; }
-    } else {
-      pos = e >> p.log2B;
-      l = e & (B - 1);
-    }
-  };
-  auto gidx = [&](int l, int pos, bool& valid) -> long long {
-    if (xax) {
-      const long long ln = line0 + l;
-      valid = ln < p.nlines;
-      return ln * n + pos;
-    }
-    const long long lo = lo0 + l;
-    valid = lo < p.stride;
-    return lo + (long long)pos * p.stride + hi * p.stride * n;
-  };
+  // the tiling of k_line_pass (TileWalk): x lines contiguous, strided tiles of B lines adjacent in x
   auto at = [&](int l, int i) -> V& { return buf[(size_t)l * Lp + fft_pad(i)]; };
 
   // load z into positions 1..n of the embedding, zero the rest.  In a product along several axes the
@@ -83,11 +64,10 @@ __device__ __forceinline__ void toeplitz_df_body(const PassParams& p, const long
   const double2* in = reinterpret_cast<const double2*>(p.in);
   const float4* zdf_in = reinterpret_cast<const float4*>(p.dfz_in);
   float4* zdf_out = reinterpret_cast<float4*>(p.dfz_out);
-  for (int e = tid; e < B * n; e += nthr) {
-    int l, pos;
-    map(e, l, pos);
-    bool valid;
-    const long long g = gidx(l, pos, valid);
+  for (TileWalk it(p, xax, tid, nthr, line0, hi, lo0); it.more(); it.next()) {
+    const int l = it.l, pos = it.pos;
+    const bool valid = it.valid;
+    const long long g = it.g;
     cdf v = zero;
     if (valid) {
       if (zdf_in) {
@@ -124,11 +104,10 @@ __device__ __forceinline__ void toeplitz_df_body(const PassParams& p, const long
   const double* D = reinterpret_cast<const double*>(p.Dr);
   const bool want_nrm = p.nrm_part != nullptr;
   double nacc = 0.0;
-  for (int e = tid; e < B * n; e += nthr) {
-    int l, pos;
-    map(e, l, pos);
-    bool valid;
-    const long long g = gidx(l, pos, valid);
+  for (TileWalk it(p, xax, tid, nthr, line0, hi, lo0); it.more(); it.next()) {
+    const int l = it.l, pos = it.pos;
+    const bool valid = it.valid;
+    const long long g = it.g;
     if (!valid) continue;
     double2 t = cdf_to(at(l, 1 + pos));
     double2 acc = accin ? accin[g] : make_double2(0.0, 0.0);
@@ -230,7 +209,7 @@ static cudaError_t launch_df_group(std::vector<PassParams>& ps, bool first, Tabl
   grids.assign(ps.size(), 0);
   for (size_t i = 0; i < ps.size(); ++i) {
     PassParams& p = ps[i];
-    if (p.L != g.L) return cudaErrorInvalidValue;
+    if (p.L != g.L || p.L != 2 * (p.n + 1)) return cudaErrorInvalidValue;  // the kernel takes n = L/2 - 1
     p.B = g.B;
     p.nt = g.nt;
     p.log2B = g.log2B;
@@ -279,6 +258,7 @@ cudaError_t run_toeplitz_df(rfnse_ctx* c, int axis, int half, bool first, const 
   p.n = c->n[axis];
   p.L = c->L[axis];
   p.log2L = c->log2L[axis];
+  if (p.L != 2 * (p.n + 1)) return cudaErrorInvalidValue;  // the kernel takes n = L/2 - 1
   p.stride = c->stride[axis];
   p.nlines = c->N / c->n[axis];
   p.tw = c->twdf[axis];
@@ -374,7 +354,7 @@ __global__ void k_df_tables(int log2L, const double* __restrict__ c64h0, const d
   fixed_twiddle_entry(log2L, kFixedLogRDF, k, R, ns, r, kk);
   double sn = 0.0, cs = 1.0;
   if (R > 1) sincospi(2.0 * (double)(r * kk) / (double)(R * ns), &sn, &cs);
-  tw[k] = cdf{dfl(cs), dfl(-sn)};
+  tw[k] = cvec<dfl>::make(dfl(cs), dfl(-sn));
   c0[k] = dfl(c64h0[k]);
   c1[k] = dfl(c64h1[k]);
 }
