@@ -74,22 +74,6 @@ __device__ __forceinline__ dfl df_split(double x) {
 }
 __device__ __forceinline__ double df_to_double(dfl a) { return df_f2d(a.hi) + df_f2d(a.lo); }
 
-// Packed float pairs (sm_100 family): one instruction applies the same FP32 operation, rounded to
-// nearest on its own, to both halves; per component the result is that of the scalar _rn operation.
-__device__ __forceinline__ float2 f2_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
-  float2 r;
-  asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
-      "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
-      "sub.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
-      : "=f"(r.x), "=f"(r.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return r;
-}
-__device__ __forceinline__ float2 f2_bcast(float v) { return make_float2(v, v); }
-
 // complex double-float, stored as the pairs hi = (re.hi, im.hi) and lo = (re.lo, im.lo), so that the
 // real and imaginary parts go through every step of an operation together as packed pairs: the same
 // operations, in the same order, as the scalar double-float arithmetic above on each part.

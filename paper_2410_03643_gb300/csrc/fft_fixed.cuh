@@ -70,21 +70,43 @@ __device__ __forceinline__ V mul_mi(V a) {  // forward W_4 = -i; inverse +i
   return INV ? cmul_i(a) : cmul_mi(a);
 }
 
+// Butterfly additions: t + d, t - d, and t +- (-i d) (forward; +i d inverse).  For FP32 each is one
+// packed pair instruction (cplx.cuh f2_*): the rotation by -i swaps the parts of d and takes its sign
+// from a multiplier of +-1 in a fused multiply-add, which rounds as the addition does.
+template <typename V> __device__ __forceinline__ V badd(V t, V d) { return cadd(t, d); }
+template <typename V> __device__ __forceinline__ V bsub(V t, V d) { return csub(t, d); }
+template <bool INV, typename V> __device__ __forceinline__ V badd_rot(V t, V d) { return cadd(t, mul_mi<INV>(d)); }
+template <bool INV, typename V> __device__ __forceinline__ V bsub_rot(V t, V d) { return csub(t, mul_mi<INV>(d)); }
+template <> __device__ __forceinline__ float2 badd<float2>(float2 t, float2 d) { return f2_add(t, d); }
+template <> __device__ __forceinline__ float2 bsub<float2>(float2 t, float2 d) { return f2_sub(t, d); }
+template <> __device__ __forceinline__ float2 badd_rot<false, float2>(float2 t, float2 d) {  // (t.x + d.y, t.y - d.x)
+  return f2_fma(make_float2(d.y, d.x), make_float2(1.f, -1.f), t);
+}
+template <> __device__ __forceinline__ float2 bsub_rot<false, float2>(float2 t, float2 d) {  // (t.x - d.y, t.y + d.x)
+  return f2_fma(make_float2(d.y, d.x), make_float2(-1.f, 1.f), t);
+}
+template <> __device__ __forceinline__ float2 badd_rot<true, float2>(float2 t, float2 d) {  // (t.x - d.y, t.y + d.x)
+  return f2_fma(make_float2(d.y, d.x), make_float2(-1.f, 1.f), t);
+}
+template <> __device__ __forceinline__ float2 bsub_rot<true, float2>(float2 t, float2 d) {  // (t.x + d.y, t.y - d.x)
+  return f2_fma(make_float2(d.y, d.x), make_float2(1.f, -1.f), t);
+}
+
 template <bool INV, typename V>
 __device__ __forceinline__ void dft2(V& a0, V& a1) {
   const V t = a0;
-  a0 = cadd(t, a1);
-  a1 = csub(t, a1);
+  a0 = badd(t, a1);
+  a1 = bsub(t, a1);
 }
 
 template <bool INV, typename V>
 __device__ __forceinline__ void dft4r(V& a0, V& a1, V& a2, V& a3) {
-  const V t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3);
-  const V t3 = mul_mi<INV>(csub(a1, a3));
-  a0 = cadd(t0, t2);
-  a2 = csub(t0, t2);
-  a1 = cadd(t1, t3);
-  a3 = csub(t1, t3);
+  const V t0 = badd(a0, a2), t1 = bsub(a0, a2), t2 = badd(a1, a3);
+  const V d = bsub(a1, a3);
+  a0 = badd(t0, t2);
+  a2 = bsub(t0, t2);
+  a1 = badd_rot<INV>(t1, d);
+  a3 = bsub_rot<INV>(t1, d);
 }
 
 // W_16^e (forward) as constants: cos/sin of multiples of pi/8
@@ -123,11 +145,10 @@ __device__ __forceinline__ void dft16(V (&v)[16]) {
   for (int n2 = 0; n2 < 4; ++n2) {
     if (ZU) {  // v[n2 + 8], v[n2 + 12] are zero
       const V a0 = v[n2], a1 = v[n2 + 4];
-      const V b1 = mul_mi<INV>(a1);
-      v[n2] = cadd(a0, a1);
-      v[n2 + 8] = csub(a0, a1);
-      v[n2 + 4] = cadd(a0, b1);
-      v[n2 + 12] = csub(a0, b1);
+      v[n2] = badd(a0, a1);
+      v[n2 + 8] = bsub(a0, a1);
+      v[n2 + 4] = badd_rot<INV>(a0, a1);
+      v[n2 + 12] = bsub_rot<INV>(a0, a1);
     } else {
       dft4r<INV>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
     }
@@ -176,11 +197,10 @@ __device__ __forceinline__ void dft_r(V (&v)[RAD]) {
   } else if constexpr (RAD == 4) {
     if (ZU) {
       const V a0 = v[0], a1 = v[1];
-      const V b1 = mul_mi<INV>(a1);
-      v[0] = cadd(a0, a1);
-      v[2] = csub(a0, a1);
-      v[1] = cadd(a0, b1);
-      v[3] = csub(a0, b1);
+      v[0] = badd(a0, a1);
+      v[2] = bsub(a0, a1);
+      v[1] = badd_rot<INV>(a0, a1);
+      v[3] = bsub_rot<INV>(a0, a1);
     } else {
       dft4r<INV>(v[0], v[1], v[2], v[3]);
     }
