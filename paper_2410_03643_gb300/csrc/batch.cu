@@ -274,7 +274,6 @@ cudaError_t build_lockstep_graph(rfnse_batch* b, int v) {
     I.Z32 = c->Z32;
     I.D = c->D;
     I.D32 = c->D32;
-    I.dfac64 = c->dfac64;
     I.dfac32 = c->dfac32;
     I.rho_dt = c->p.rho * c->p.dt;
     I.omega = c->p.omega;

@@ -177,13 +177,17 @@ __global__ void k_tu_from_residual(const double* __restrict__ D, const double2* 
 
 // One steady step's pointwise set-up in the mixed form, with T u^{n-1} cached: D = rho dt |u^n|^2
 // (as k_diag), the right-hand side f = u^{n-1} - i (T u^{n-1} - D u^{n-1}) (paper Sec. 2, the block
-// form's f = -i b with b = (T - D + iI) u^{n-1}) and the tables of k_prep_D, in one sweep.
+// form's f = -i b with b = (T - D + iI) u^{n-1}) and the tables of k_prep_D, in one sweep.  With
+// dfac64 null (the mixed form's solves read only the FP32 tables) the FP32 factor is computed in
+// FP32: the FP64 division per point made this sweep FP64-bound (GB300 issues two FP64 FMAs per SM and
+// cycle), and the preconditioner needs the factor only to FP32 accuracy.
 __global__ void k_step_prep(const double2* __restrict__ uc, const double2* __restrict__ up,
                             const double2* __restrict__ Tup, double* __restrict__ D, double2* __restrict__ f,
                             float* __restrict__ D32, double2* __restrict__ dfac64, float2* __restrict__ dfac32,
                             double rho_dt, double omega, long long N, double* __restrict__ nrm_part) {
   __shared__ double sh[32];
   const double w1 = omega + 1.0, two_w = 2.0 * omega;
+  const float w1f = (float)w1, two_wf = (float)two_w;
   double nacc = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     const double2 v = uc[i], uv = up[i], tv = Tup[i];
@@ -194,11 +198,17 @@ __global__ void k_step_prep(const double2* __restrict__ uc, const double2* __res
     f[i] = fv;
     nacc = fma(fv.x, fv.x, nacc);
     nacc = fma(fv.y, fv.y, nacc);
-    const double s = two_w / (w1 * w1 + d * d);
-    const double2 fac = make_double2(s * w1, s * d);
-    D32[i] = (float)d;
-    dfac64[i] = fac;
-    dfac32[i] = make_float2((float)fac.x, (float)fac.y);
+    const float df = (float)d;
+    D32[i] = df;
+    if (dfac64) {
+      const double s = two_w / (w1 * w1 + d * d);
+      const double2 fac = make_double2(s * w1, s * d);
+      dfac64[i] = fac;
+      dfac32[i] = make_float2((float)fac.x, (float)fac.y);
+    } else {
+      const float sf = two_wf / fmaf(df, df, w1f * w1f);
+      dfac32[i] = make_float2(sf * w1f, sf * df);
+    }
   }
   if (nrm_part) {  // this block's share of ||f||^2 for the solve's norm kernel (uniform branch)
     nacc = block_sum(nacc, sh);
@@ -306,7 +316,8 @@ int step_prep_blocks(long long N) { return (int)ew_blocks(N); }
 void launch_step_prep(rfnse_ctx* c, const double2* uc, const double2* up, const double2* Tup, cudaStream_t s,
                       double* nrm_part) {
   count_launch();
-  k_step_prep<<<ew_blocks(c->N), 256, 0, s>>>(uc, up, Tup, c->D, c->f, c->D32, c->dfac64, c->dfac32,
+  k_step_prep<<<ew_blocks(c->N), 256, 0, s>>>(uc, up, Tup, c->D, c->f, c->D32,
+                                              c->p.precision == 1 ? nullptr : c->dfac64, c->dfac32,
                                               c->p.rho * c->p.dt, c->p.omega, c->N, nrm_part);
 }
 void launch_zero(double2* x, long long N, cudaStream_t s) { k_zero<<<ew_blocks(N), 256, 0, s>>>(x, N); }

@@ -39,8 +39,8 @@ __device__ __forceinline__ int ew_item(const LockInst* __restrict__ li, int n, l
 }
 
 // Steady step set-up of every instance (the mixed form's k_step_prep): D = rho dt |u^n|^2,
-// f = u^{n-1} - i (T u^{n-1} - D u^{n-1}), the (omega I + D) sub-solve tables, x = 0, and the block
-// partials of ||f||^2.
+// f = u^{n-1} - i (T u^{n-1} - D u^{n-1}), the FP32 (omega I + D) sub-solve tables, x = 0, and the
+// block partials of ||f||^2.
 __global__ void __launch_bounds__(kLockEwThreads) k_ls_step_prep(const LockInst* __restrict__ li, int n,
                                                                   unsigned long long* counts) {
   __shared__ double sh[32];
@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(kLockEwThreads) k_ls_step_prep(const LockInst*
   long long lb;
   const LockInst& I = li[ew_item(li, n, lb)];
   const long long N = I.N, nb = I.nblk;
-  const double rho_dt = I.rho_dt, w1 = I.omega + 1.0, two_w = 2.0 * I.omega;
+  const double rho_dt = I.rho_dt;
+  const float w1f = (float)(I.omega + 1.0), two_wf = (float)(2.0 * I.omega);
   const double2* __restrict__ uc = I.u_cur;
   const double2* __restrict__ up = I.u_prev;
   const double2* __restrict__ tp = I.Tu_prev;
@@ -62,11 +63,10 @@ __global__ void __launch_bounds__(kLockEwThreads) k_ls_step_prep(const LockInst*
     I.f[i] = fv;
     nacc = fma(fv.x, fv.x, nacc);
     nacc = fma(fv.y, fv.y, nacc);
-    const double s = two_w / (w1 * w1 + d * d);
-    const double2 fac = make_double2(s * w1, s * d);
-    I.D32[i] = (float)d;
-    I.dfac64[i] = fac;
-    I.dfac32[i] = make_float2((float)fac.x, (float)fac.y);
+    const float df = (float)d;
+    const float sf = two_wf / fmaf(df, df, w1f * w1f);  // FP32: the batch's solves read the FP32 tables only
+    I.D32[i] = df;
+    I.dfac32[i] = make_float2(sf * w1f, sf * df);
     I.x[i] = make_double2(0.0, 0.0);
   }
   nacc = block_sum_c(nacc, sh);

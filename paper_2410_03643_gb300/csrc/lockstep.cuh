@@ -37,7 +37,6 @@ struct LockInst {
   float2* Z32;              // preconditioned basis (FP32, N-strided)
   double* D;
   float* D32;
-  double2* dfac64;
   float2* dfac32;
   double rho_dt, omega;
   double* nrm_f;            // partials of ||f||^2 (one per element-wise block)
