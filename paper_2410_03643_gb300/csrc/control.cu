@@ -7,6 +7,7 @@
 #include <cmath>
 #include "internal.cuh"
 #include "coop.cuh"
+#include "dfloat.cuh"
 
 namespace rfnse {
 
@@ -338,8 +339,8 @@ __global__ void k_combine_f32_add_dev(const float2* __restrict__ Z, long long ld
     double2 a = x[i];
     for (int q = 0; q < k; ++q) {
       const float2 v = Z[(size_t)q * ldz + i];
-      a.x += y[q] * (double)v.x;
-      a.y += y[q] * (double)v.y;
+      a.x += y[q] * df_f2d(v.x);  // exact, without an FP64-pipe conversion
+      a.y += y[q] * df_f2d(v.y);
     }
     x[i] = a;
   }

@@ -7,6 +7,7 @@
 #include <string>
 #include "internal.cuh"
 #include "cplx.cuh"
+#include "dfloat.cuh"
 
 namespace rfnse {
 
@@ -118,8 +119,8 @@ __global__ void k_combine_f32_add(const float2* __restrict__ Z, long long ldz, c
     double2 a = x[i];
     for (int q = 0; q < k; ++q) {
       const float2 v = Z[(size_t)q * ldz + i];
-      a.x += y[q] * (double)v.x;
-      a.y += y[q] * (double)v.y;
+      a.x += y[q] * df_f2d(v.x);  // exact, without an FP64-pipe conversion
+      a.y += y[q] * df_f2d(v.y);
     }
     x[i] = a;
   }

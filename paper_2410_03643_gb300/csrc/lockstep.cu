@@ -7,6 +7,7 @@
 #include <cmath>
 #include "internal.cuh"
 #include "coop.cuh"
+#include "dfloat.cuh"
 #include "lockstep.cuh"
 
 namespace rfnse {
@@ -287,8 +288,8 @@ __global__ void __launch_bounds__(kLockEwThreads) k_ls_combine_add(const LockIns
     double2 a = I.x[i];
     for (int q = 0; q < k; ++q) {
       const float2 v = I.Z32[(size_t)q * N + i];
-      a.x += y[q] * (double)v.x;
-      a.y += y[q] * (double)v.y;
+      a.x += y[q] * df_f2d(v.x);  // exact, without an FP64-pipe conversion
+      a.y += y[q] * df_f2d(v.y);
     }
     I.x[i] = a;
   }
