@@ -163,6 +163,8 @@ def parse():
                          "the grid-wide kernel, -8 / -16 one cluster of that many CTAs; 0 = as tuned)")
     ap.add_argument("--no-lockstep", action="store_true",
                     help="batches run one CUDA graph branch per instance instead of the lock-step launches")
+    ap.add_argument("--lockstep", action="store_true",
+                    help="batches run in lock-step even below the default instance count (mixed form)")
     ap.add_argument("--no-3d", action="store_true",
                     help="default 2d workload: leave out the 3-D 255^3 half of the metric (config_3d)")
     ap.add_argument("--kernel-case", default=None, choices=["2d", "3d"],
@@ -492,6 +494,8 @@ def measure(args, env: Env, name: str, instances: int, steps: int, warmup: int, 
             b = rfnse.Batch([p for p, _ in inst], precision=precision, stream=main, device_loop=device_loop)
             if args.no_lockstep and b.lockstep:
                 b.set_lockstep(False)
+            if args.lockstep and not b.lockstep and precision == 1:
+                b.set_lockstep(True)
             if not args.no_autotune:
                 nc, ch = b.autotune(reps=5)
                 tuning.setdefault(precision, {"configs": nc, "changed": ch,
