@@ -102,14 +102,14 @@ PROFILED = {
 # capture was taken: once a source has changed the figure no longer describes the kernel and the line
 # reports traffic null.
 TRAFFIC = {
-    ("2d", "arnoldi"): (10513216, "15694035f486"),
+    ("2d", "arnoldi"): (10512064, "2f0ff00eb74a"),
     ("2d", "fp32_fused_x"): (5277952, "bc9364c29794"),
     ("2d", "fp32_dst"): (4206848, "bc9364c29794"),
     ("2d", "fp32_dst_lam"): (4212480, "bc9364c29794"),
     ("2d", "fp32_toep_acc"): (8398976, "bc9364c29794"),
     ("2d", "df_toep_x"): (6342912, "dcc06e68e64c"),
     ("2d", "df_toep_acc"): (8433408, "dcc06e68e64c"),
-    ("3d", "arnoldi"): (1814097400, "15694035f486"),
+    ("3d", "arnoldi"): (1813218440, "2f0ff00eb74a"),
     ("3d", "fp32_fused_x"): (555763840, "bc9364c29794"),
     ("3d", "fp32_dst"): (349960619, "bc9364c29794"),
     ("3d", "fp32_dst_lam"): (370098944, "bc9364c29794"),

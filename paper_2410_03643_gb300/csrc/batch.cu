@@ -430,7 +430,7 @@ long long solve_kernels(const rfnse_ctx* c, const GmresPeek& pk) {
   const int d = c->d;
   const int mixed = c->p.precision == 1;
   const long long step_k = (d == 1 ? 1 : 3 * d - 2) + 1;
-  const long long cycle_k = mixed ? 1 + 1 + 1 + 1 + d + 1 + 1 : 1 + 1 + 1 + (d == 1 ? 1 : 2 * d - 1) + d + 1;
+  const long long cycle_k = mixed ? 1 + 1 + d + 1 + 1 : 1 + 1 + 1 + (d == 1 ? 1 : 2 * d - 1) + d + 1;
   const long long cycles = mixed ? pk.outer : (pk.it > 0 ? pk.outer + 1 : 0);
   return 2 + step_k * pk.it + cycle_k * cycles;
 }

@@ -275,7 +275,7 @@ __global__ void k_combine_dev(const double2* __restrict__ V, long long ldv, cons
 // symmetric).  Used only when beta <= kUpdRatio tol ||f||, so that this error stays a small fraction
 // of tol ||f||; it is also added to the stopping test.  k < 0: k = gs->j and the decision is taken
 // here; otherwise upd and err come from the host.
-__global__ void k_resid_coeffs(GmresState* gs, int k_in, int upd_in, double err_in, double tol) {
+__device__ __forceinline__ void resid_coeffs_body(GmresState* gs, int k_in, int upd_in, double err_in, double tol) {
   const int k = k_in >= 0 ? k_in : gs->j;
   int upd;
   double err;
@@ -295,6 +295,42 @@ __global__ void k_resid_coeffs(GmresState* gs, int k_in, int upd_in, double err_
     t = -gs->sn[i] * t;
   }
   gs->q[0] = t;
+}
+__global__ void k_resid_coeffs(GmresState* gs, int k_in, int upd_in, double err_in, double tol) {
+  resid_coeffs_body(gs, k_in, upd_in, err_in, tol);
+}
+
+// Mixed form, end of a refinement cycle of k = gs->j flexible Arnoldi steps, in one launch (in place of
+// the back-substitution, the solution update and the recurrence's coefficients as three): thread 0 of
+// every block solves R y = g on the leading k x k triangle into shared memory (the operations of
+// k_backsolve_dev, in its order), block 0 stores y and takes the recurrence's decision and
+// coefficients (k_resid_coeffs), and every block adds its share of sum_q y_q Z_q to x.
+__global__ void k_cycle_end_mixed(const float2* __restrict__ Z, long long ldz, GmresState* gs,
+                                  double2* __restrict__ x, long long N, double tol) {
+  __shared__ double y[kMaxM];
+  const int k = gs->j;
+  if (threadIdx.x == 0) {
+    const int ld = kMaxM + 1;
+    for (int i = k - 1; i >= 0; --i) {
+      double s = gs->g[i];
+      for (int jj = i + 1; jj < k; ++jj) s -= gs->H[(size_t)jj * ld + i] * y[jj];
+      y[i] = s / gs->H[(size_t)i * ld + i];
+    }
+  }
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    for (int t = threadIdx.x; t < k; t += blockDim.x) gs->y[t] = y[t];
+    if (threadIdx.x == 0) resid_coeffs_body(gs, -1, -1, 0.0, tol);
+  }
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    double2 a = x[i];
+    for (int q = 0; q < k; ++q) {
+      const float2 v = Z[(size_t)q * ldz + i];
+      a.x += y[q] * df_f2d(v.x);  // exact, without an FP64-pipe conversion
+      a.y += y[q] * df_f2d(v.y);
+    }
+    x[i] = a;
+  }
 }
 
 // r = sum_{i<k} q_i V_i + q_k inv_h w when gs->upd, k = gs->j if k_in < 0; with nrm_part, each
@@ -526,6 +562,11 @@ void launch_combine_f32_add_dev(const float2* Z, long long ldz, const GmresState
                                 cudaStream_t s) {
   count_launch();
   k_combine_f32_add_dev<<<ew_blocks_c(N), 256, 0, s>>>(Z, ldz, gs, x, N);
+}
+void launch_cycle_end_mixed(const float2* Z, long long ldz, GmresState* gs, double2* x, long long N, double tol,
+                            cudaStream_t s) {
+  count_launch();
+  k_cycle_end_mixed<<<ew_blocks_c(N), 256, 0, s>>>(Z, ldz, gs, x, N, tol);
 }
 void launch_resid_coeffs(GmresState* gs, int k, int upd, double err, double tol, cudaStream_t s) {
   count_launch();

@@ -150,6 +150,10 @@ void launch_norm_ctl(const double2* x, GmresState* gs, long long N, int blocks, 
 void launch_cycle_begin(GmresState* gs, const SolveCfg& cfg, cudaGraphConditionalHandle h_inner,
                         cudaGraphConditionalHandle h_outer, int set_cond, cudaStream_t s);
 void launch_backsolve_dev(GmresState* gs, cudaStream_t s);
+// Mixed form, end of a refinement cycle (graph form): back-substitution, x += Z y and the residual
+// recurrence's decision and coefficients in one launch (control.cu k_cycle_end_mixed).
+void launch_cycle_end_mixed(const float2* Z, long long ldz, GmresState* gs, double2* x, long long N, double tol,
+                            cudaStream_t s);
 // Mixed form, end of a refinement cycle of k Arnoldi steps (k < 0: gs->j).  Decides whether the new
 // residual is formed from the Arnoldi basis (upd < 0: on the device, when the cycle's starting
 // residual beta <= kUpdRatio * tol * ||f||; otherwise upd as given) and, if so, stores its

@@ -427,10 +427,8 @@ cudaError_t capture_solve(rfnse_ctx* c, int mixed, int half, cudaGraph_t g, cuda
     return fail(e);
   launch_cycle_begin(c->gs, cfg, hi, ho, 1, bs);
   if ((e = add_while_node(bs, hi, &ibody)) != cudaSuccess) return fail(e);
-  launch_backsolve_dev(c->gs, bs);
   if (mixed) {
-    launch_combine_f32_add_dev(c->Z32, N, c->gs, c->x, N, bs);
-    launch_resid_coeffs(c->gs, -1, -1, 0.0, cfg.tol, bs);
+    launch_cycle_end_mixed(c->Z32, N, c->gs, c->x, N, cfg.tol, bs);
     // the residual (product or recurrence, whichever runs) leaves the partials of ||r||^2
     double* part_df = c->nrm_part + kNormPartMax;
     double* part_upd = c->nrm_part + 2 * kNormPartMax;
@@ -441,6 +439,7 @@ cudaError_t capture_solve(rfnse_ctx* c, int mixed, int half, cudaGraph_t g, cuda
     launch_norm_ctl(c->r, c->gs, N, c->red_blocks, c->partials, c->counter, c->bar, cfg, 2, ho, 1, bs, part_upd,
                     resid_update_blocks(N), part_df, c->nrm_df_blocks);
   } else {
+    launch_backsolve_dev(c->gs, bs);
     launch_combine_dev(c->V, N, c->gs, c->r, N, bs);
     if ((e = run_precon<double, double2, double2, double2, double2, false, false>(
              c, c->r, nullptr, nullptr, c->x, 1, c->D, nullptr, nullptr, nullptr, kOne, kI, half, c->t1, c->t2)) !=
@@ -511,7 +510,7 @@ static rfnse_status solve_graph(rfnse_ctx* c, const double* D, const double2* f,
      // per cycle the cycle start, back-substitution, update and residual kernels
     const int d = c->d;
     const long long step_k = (d == 1 ? 1 : 3 * d - 2) + 1;
-    const long long cycle_k = mixed ? 1 + 1 + 1 + 1 + d + 1 + 1 : 1 + 1 + 1 + (d == 1 ? 1 : 2 * d - 1) + d + 1;
+    const long long cycle_k = mixed ? 1 + 1 + d + 1 + 1 : 1 + 1 + 1 + (d == 1 ? 1 : 2 * d - 1) + d + 1;
     const long long cycles = mixed ? pk.outer : (pk.it > 0 ? pk.outer + 1 : 0);
     count_launch(2 + step_k * pk.it + cycle_k * cycles);
   }
