@@ -57,6 +57,7 @@ METRIC = "DOF*timesteps/s"
 UNIT = "DOF*timesteps/s"
 FP64_ALU_PEAK_FLOPS = 152 * 2 * 2 * 2.07e9   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 FP32_ALU_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9  # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
+NOMINAL_HBM_GBS = 7900.0                      # GB300 HBM3e nominal bandwidth (context beside the measured copy)
 CSRC = os.path.join(ROOT, "paper_2410_03643_gb300", "csrc")
 
 
@@ -449,12 +450,15 @@ def roofline_entry(name: str, cls: str, prof, ms_serial: float, nprof: int):
         achieved = fl / (pms * 1e-3) / 1e12
         e.update({"bound": "alu", "achieved": achieved, "peak": FP64_ALU_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
                   "frac": achieved * 1e12 / FP64_ALU_PEAK_FLOPS, "achieved_GBs": gbs, "frac_of_hbm": gbs / hbm,
+                  "traffic_GBs": traffic * n / (pms * 1e-3) / 1e9 if traffic is not None else None,
                   "peak_note": "FP64 FMA issue rate: 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz = 1.26 TFLOP/s "
                                "(bench.py --alu-probe measures it); the algorithmic FP64 flops per launch "
                                "(8 (j + 1) + 4 per point) need more time at that rate than its bytes at the "
                                f"copy bandwidth ({how}, beside it)"})
     else:
         e.update({"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                  "frac_of_nominal_hbm": gbs / NOMINAL_HBM_GBS,
+                  "traffic_GBs": traffic * n / (pms * 1e-3) / 1e9 if traffic is not None else None,
                   "achieved_TFLOPs": fl / (pms * 1e-3) / 1e12,
                   "peak_note": f"copy bandwidth, {how} (MEASURED_PEAKS.json); algorithmic bytes = every "
                                "operand read once and every result written once"})
